@@ -11,7 +11,8 @@ Per op of the program (`oracle.circuit.build_program`):
     (control, target) over I, X, Y, Z, skipping II) non-identity Paulis.
   * Crosstalk exp(-i theta Q) (Eq. 4, sign reading exp(-i theta Q)):
     P' = C^dag Q C, then cos(theta) I - i sin(theta) P' on the MPS as a
-    bond-2 MPO, then compression (Sec. IV B).
+    bond-2 MPO, then compression (Sec. IV B) over the support of P' widened
+    to include the orthogonality centre (`sweep_span`).
   * Z measurement of qubit q (Sec. IV A: a Pauli pushed through C and applied
     to the tensor network): P' = C^dag Z_q C, e = <phi|P'|phi>,
     p0 = (1 + e)/2, outcome b = 0 iff u < p0.
@@ -135,6 +136,15 @@ class ShotSim:
             self.T.left_pauli("X", [q])
 
     # -- non-Clifford and measurement ------------------------------------------
+    def sweep_span(self, lo, hi):
+        """Sites swept by the compression after an operator on [lo, hi]: the
+        support plus every site up to the orthogonality centre, so that the
+        sites left of the sweep are left-canonical and those right of it
+        right-canonical (Sec. IV B leaves the sweep extent open; covering the
+        centre replaces separate gauge moves)."""
+        c = self.mps.center
+        return min(lo, c), max(hi, c)
+
     def rotation(self, k):
         pair = self.prog.pairs[k]
         q = Pauli.identity(self.n)
@@ -147,11 +157,11 @@ class ShotSim:
         th = float(self.theta[k])
         supp = pp.support()
         lo, hi = int(supp.min()), int(supp.max())
-        self.mps.move_center_into(lo, hi)
+        a, b = self.sweep_span(lo, hi)
         ops1 = {int(s): pp.site_matrix(s) for s in supp}
         w1 = -1j * math.sin(th) * (1j ** pp.m)
         self.mps.apply_two_branch(lo, hi, {}, ops1, math.cos(th), w1)
-        self._compress(lo, hi, "rot")
+        self._compress(a, b, "rot")
 
     def measure(self, q, ev_b, ev_f, rec, reset, ev_r):
         zq = Pauli.single(self.n, q, "Z")
@@ -168,11 +178,11 @@ class ShotSim:
         pb = p0 if b == 0 else 1.0 - p0
         self.born[rec] = pb
         self.logp += math.log(pb) if pb > 0 else -math.inf
-        self.mps.move_center_into(lo, hi)
+        sa, sb = self.sweep_span(lo, hi)
         if not pp.x.any():
             w1 = (1 if b == 0 else -1) * (1j ** pp.m) * 0.5
             self.mps.apply_two_branch(lo, hi, {}, ops, 0.5, w1)
-            self._compress(lo, hi, "measA")
+            self._compress(sa, sb, "measA")
         else:
             j = int(np.flatnonzero(pp.x)[0])
             letters = pp.letters()
@@ -187,7 +197,7 @@ class ShotSim:
             self.mps.apply_two_branch(lo, hi, ops0, ops1, 1.0, 1.0)
             v = EIGVEC[key]
             self.mps.apply_site(j, np.outer(np.array([1, 0], dtype=complex), v.conj()))
-            self._compress(lo, hi, "measB")
+            self._compress(sa, sb, "measB")
             for s in supp:
                 s = int(s)
                 if s != j:

@@ -32,8 +32,10 @@ class Workload:
     p2_scale: float = 1.0
     pR_scale: float = 2.0
     pM_scale: float = 5.0
-    svd_cutoff: float = 1e-14
-    degeneracy_tol: float = 1e-9
+    # Schmidt values at or below svd_cutoff * s_1 are dropped; at a chi cap,
+    # kept values must exceed the first dropped one by degeneracy_tol * s_1.
+    svd_cutoff: float = 1e-6
+    degeneracy_tol: float = 1e-6
     pair_rule: str = "adjacent_idle"
     theta_sigma: float = 0.0
     theta_seed: int = 7
@@ -86,6 +88,6 @@ D5_BENCH = Workload(
     precision=PRECISION_C64,
     shots=16384,
     seed=0,
-    svd_cutoff=1e-6,
-    degeneracy_tol=1e-5,
+    svd_cutoff=1e-3,
+    degeneracy_tol=1e-4,
 )
