@@ -1,0 +1,175 @@
+/*
+ * stn.h — C ABI of a GB300 (sm_103a) stabilizer-tensor-network simulator of
+ * noisy rotated-surface-code syndrome extraction under coherent crosstalk.
+ *
+ * Method (Harper, Nakhl, Sevior, Usman, "Non-Clifford Crosstalk Noise in
+ * Surface Codes Using Hybrid Stabilizer-Tensor Network Methods"):
+ *   - each shot is |psi> = C |MPS> (Eq. 7): a Clifford frame C held as an
+ *     inverse tableau, times a matrix product state;
+ *   - Clifford gates and Pauli noise (Eq. 2-3, Table I) update C only;
+ *   - a crosstalk rotation exp(-i theta P) (Eq. 4) and a Pauli measurement are
+ *     pushed through C (Sec. IV A) and applied to the MPS as a bond-2 Pauli
+ *     MPO, followed by truncation to a bond-dimension cap (Sec. IV B, Eq. 8);
+ *   - the surface code layout and the Z/X syndrome circuits are those of
+ *     Sec. II and Fig. 1, repeated for `rounds` rounds.
+ *
+ * Conventions shared by every call:
+ *   - All pointers named h_* are host memory owned by the caller; d_* are
+ *     device memory owned by the caller.  The context owns all other device
+ *     memory (tableaux, MPS arenas, scratch) and frees it in stn_destroy.
+ *   - Every call returns a stn_status and never aborts.  On failure the
+ *     reason is kept in the context (stn_last_error).  Device-side failures
+ *     (arena overflow, non-finite numbers) are recorded on the device and
+ *     reported by the next call that synchronises (stn_sync, stn_read_*).
+ *   - A context is bound to one CUDA stream (given at creation) and is not
+ *     thread-safe.  Work is enqueued on that stream; calls that return host
+ *     data synchronise it.
+ *   - Shot s of a batch started at `shot_offset` draws every random number
+ *     from Philox4x32-10 (Salmon et al., SC'11) with key = seed and counter =
+ *     (global shot index, event id), so batches and shards are reproducible
+ *     and independent of batch size.
+ */
+#ifndef STN_H
+#define STN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stn_ctx stn_ctx;
+
+typedef enum {
+  STN_OK = 0,
+  STN_EINVAL = 1,   /* invalid argument or configuration */
+  STN_ENOMEM = 2,   /* device allocation failed */
+  STN_ECUDA = 3,    /* CUDA runtime error */
+  STN_ETIMEOUT = 4, /* a bounded device wait ran out */
+  STN_ENUMERIC = 5, /* non-finite or vanishing norm in the MPS */
+  STN_ENOTIMPL = 6, /* entry point not implemented */
+  STN_EOVERFLOW = 7 /* a device arena was too small */
+} stn_status;
+
+enum { STN_PAIRS_ADJACENT_IDLE = 0, STN_PAIRS_ADJACENT_IDLE_DIAG_XX = 1 };
+enum { STN_PRECISION_C128 = 0, STN_PRECISION_C64 = 1 };
+
+/* Simulation parameters.  Rates follow Table I: p1 = p1_scale*p after each
+ * single-qubit gate (Eq. 2), p2 = p2_scale*p after each CNOT (Eq. 3),
+ * pR = pR_scale*p X flip after each reset, pM = pM_scale*p flip of each
+ * recorded bit. */
+typedef struct {
+  int32_t distance;      /* code distance d >= 3, odd; n = 2 d^2 - 1 qubits */
+  int32_t rounds;        /* syndrome rounds >= 1 */
+  int32_t pair_rule;     /* STN_PAIRS_*: which pairs get crosstalk (Sec. III B) */
+  int32_t chi_cap;       /* bond-dimension cap chi_max (Sec. IV B), 1..256 */
+  double p, p1_scale, p2_scale, pR_scale, pM_scale;
+  double svd_cutoff;     /* drop Schmidt values <= svd_cutoff * s_1 */
+  double degeneracy_tol; /* at the cap, kept values exceed the first dropped
+                            one by more than degeneracy_tol * s_1 */
+  int32_t precision;     /* STN_PRECISION_*: arithmetic of the MPS path */
+  uint64_t seed;         /* Philox key */
+} stn_config;
+
+/* Per-shot diagnostics of the last batch (Sec. IV B: truncation). */
+typedef struct {
+  int32_t max_chi;   /* largest bond dimension reached */
+  int32_t near_draws; /* Born draws with |u - p0| < 1e-5 */
+  double discarded;  /* sum over truncations of the discarded weight */
+  double logp;       /* log-probability of the realised outcomes */
+} stn_shot_stats;
+
+/* Compile the program (layout, CNOT schedule, crosstalk pairs, event ids) and
+ * allocate device state for up to max_shots shots per batch.  `cuda_stream`
+ * is a cudaStream_t (NULL = legacy default stream).  On success *out owns
+ * the context.  Errors: STN_EINVAL (bad config), STN_ENOMEM, STN_ECUDA. */
+stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_stream,
+                      stn_ctx **out);
+void stn_destroy(stn_ctx *ctx);
+const char *stn_last_error(const stn_ctx *ctx);
+
+/* Sizes of the compiled program: qubits, crosstalk pairs K (the length of
+ * every theta table), measurement records per shot, random events per shot,
+ * ops per shot. */
+int32_t stn_num_qubits(const stn_ctx *ctx);
+int32_t stn_num_pairs(const stn_ctx *ctx);
+int32_t stn_num_meas(const stn_ctx *ctx);
+int32_t stn_num_events(const stn_ctx *ctx);
+int32_t stn_num_ops(const stn_ctx *ctx);
+
+/* Copy the compiled program to the host: ops[i] = {kind, a, b, pauli, ev, idx}
+ * as six int32 per op (kinds: 1 reset flip, 2 H, 3 1q noise, 4 CNOT,
+ * 5 2q noise, 6 rotation, 7 Z measurement; for 7, pauli = 1 when the qubit
+ * is reset afterwards), and pairs[k] = {a, b, pauli(0 ZZ, 1 XX), layer_mask}.
+ * Either pointer may be NULL. */
+stn_status stn_get_program(const stn_ctx *ctx, int32_t *h_ops, int32_t *h_pairs);
+
+/* Host-only (no GPU needed): compile the program of `cfg` and report its
+ * sizes h_counts[5] = {qubits, pairs K, measurements, events, ops}; when
+ * h_ops / h_pairs are not NULL, also copy the ops and pairs as in
+ * stn_get_program (the caller sizes them from a first call with NULL).
+ * Errors: STN_EINVAL for a bad config. */
+stn_status stn_compile_program(const stn_config *cfg, int32_t *h_counts, int32_t *h_ops,
+                               int32_t *h_pairs);
+
+/* Start a batch of `shots` shots (<= max_shots) with global indices
+ * shot_offset .. shot_offset+shots-1: every tableau is reset to the identity
+ * frame and every MPS to |0...0>.  Asynchronous. */
+stn_status stn_begin_batch(stn_ctx *ctx, int64_t shots, uint64_t shot_offset);
+
+/* Apply program segment `round` to every shot of the batch, with per-pair
+ * crosstalk angles h_theta[K] (host, radians).  Segments are 0..rounds:
+ * segment 0 holds the initial resets and syndrome round 0, segment r the
+ * syndrome round r, segment `rounds` the final Z readout of the data qubits.
+ * One persistent kernel launch per segment.  Asynchronous. */
+stn_status stn_apply_round(stn_ctx *ctx, int32_t round, const double *h_theta);
+
+/* Same, with the angles already in device memory (d_theta[K], doubles). */
+stn_status stn_apply_round_device(stn_ctx *ctx, int32_t round, const double *d_theta);
+
+/* Wait for the stream and report any device-side failure of the batch. */
+stn_status stn_sync(stn_ctx *ctx);
+
+/* Copy results of the current batch to the host (synchronises).
+ * h_records: [shots][ceil(n_meas/8)] bytes, bit i of record j at byte i/8,
+ * bit i%8; h_born: [shots][n_meas] realised Born probabilities (or NULL);
+ * h_stats: [shots] (or NULL). */
+stn_status stn_read_records(stn_ctx *ctx, uint8_t *h_records, double *h_born,
+                            stn_shot_stats *h_stats);
+
+/* Device pointer to the packed records of the current batch
+ * ([shots][ceil(n_meas/8)] bytes, owned by the context). */
+const uint8_t *stn_device_records(const stn_ctx *ctx);
+
+/* Inverse tableau of one shot of the current batch (synchronises): rows
+ * X_0..X_{n-1}, Z_0..Z_{n-1}; row r is i^phase[r] X^x Z^z with x bits in
+ * h_x[r*W .. r*W+W-1] (W = ceil(n/64) words, qubit q at bit q%64 of word
+ * q/64), likewise h_z.  h_phase[r] in 0..3. */
+stn_status stn_read_tableau(stn_ctx *ctx, int64_t shot, uint64_t *h_x, uint64_t *h_z,
+                            uint8_t *h_phase);
+
+/* Bond dimensions chi_0..chi_{n-2} of one shot's MPS (synchronises). */
+stn_status stn_read_bonds(stn_ctx *ctx, int64_t shot, int32_t *h_bonds);
+
+/* Whole job: begin_batch, every segment with h_theta, read_records. */
+stn_status stn_sample_shots(stn_ctx *ctx, int64_t shots, uint64_t shot_offset,
+                            const double *h_theta, uint8_t *h_records, double *h_born,
+                            stn_shot_stats *h_stats);
+
+/* Gradient of log P(fixed record) with respect to the K crosstalk angles.
+ * Not implemented: returns STN_ENOTIMPL. */
+stn_status stn_logprob_grad(stn_ctx *ctx, const uint8_t *h_records, int64_t n_rec,
+                            const double *h_theta, double *h_logp, double *h_grad);
+
+/* Philox4x32-10 uniforms u = ((w0<<21) ^ (w1>>11)) * 2^-53 for shots
+ * shot_offset.. (n_shots) and events event_offset.. (n_events), written to
+ * device memory d_out[n_shots][n_events] on `cuda_stream`.  Stateless. */
+stn_status stn_philox_uniforms(uint64_t seed, uint64_t shot_offset, int64_t n_shots,
+                               uint32_t event_offset, int32_t n_events, double *d_out,
+                               void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STN_H */

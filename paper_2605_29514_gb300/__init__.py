@@ -1,0 +1,177 @@
+"""GB300 (sm_103a) stabilizer-tensor-network simulator of noisy surface-code
+syndrome extraction under coherent crosstalk.
+
+Python binding of the C ABI in include/stn.h.  The binding marshals arguments
+only; tableau updates, Pauli conjugation, MPS apply/compress, Born sampling and
+Philox draws all run in the library's CUDA kernels.  There is no CPU fallback:
+without the built library every call raises.
+"""
+
+import ctypes
+
+import numpy as np
+
+from ._native import Config, ShotStats, build, load
+
+STN_OK, STN_EINVAL, STN_ENOMEM, STN_ECUDA, STN_ETIMEOUT, STN_ENUMERIC, STN_ENOTIMPL, STN_EOVERFLOW = range(8)
+PAIR_RULES = {"adjacent_idle": 0, "adjacent_idle+diag_xx": 1}
+OP_KINDS = {1: "RN", 2: "H", 3: "D1", 4: "CX", 5: "D2", 6: "ROT", 7: "M"}
+
+
+class StnError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"stn status {status}: {message}")
+        self.status = status
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def config_from_workload(w):
+    return Config(
+        distance=w.distance, rounds=w.rounds, pair_rule=PAIR_RULES[w.pair_rule], chi_cap=w.chi_cap,
+        p=w.p, p1_scale=w.p1_scale, p2_scale=w.p2_scale, pR_scale=w.pR_scale, pM_scale=w.pM_scale,
+        svd_cutoff=w.svd_cutoff, degeneracy_tol=w.degeneracy_tol, precision=w.precision,
+        seed=w.seed)
+
+
+class Simulator:
+    """One stn_ctx: a compiled program plus device state for max_shots shots."""
+
+    def __init__(self, workload, max_shots, stream=0):
+        self.lib = load()
+        self.cfg = config_from_workload(workload)
+        ctx = ctypes.c_void_p()
+        st = self.lib.stn_create(ctypes.byref(self.cfg), int(max_shots), ctypes.c_void_p(stream),
+                                 ctypes.byref(ctx))
+        if st != STN_OK:
+            raise StnError(st, "stn_create failed")
+        self.ctx = ctx
+        self.max_shots = int(max_shots)
+        self.n_qubits = self.lib.stn_num_qubits(ctx)
+        self.n_pairs = self.lib.stn_num_pairs(ctx)
+        self.n_meas = self.lib.stn_num_meas(ctx)
+        self.n_events = self.lib.stn_num_events(ctx)
+        self.n_ops = self.lib.stn_num_ops(ctx)
+        self.rounds = workload.rounds
+        self.rec_bytes = (self.n_meas + 7) // 8
+        self.words = (self.n_qubits + 63) // 64
+        self.shots = 0
+
+    def _check(self, st):
+        if st != STN_OK:
+            msg = self.lib.stn_last_error(self.ctx)
+            raise StnError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.stn_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def program(self):
+        ops = np.zeros((self.n_ops, 6), dtype=np.int32)
+        pairs = np.zeros((max(self.n_pairs, 1), 4), dtype=np.int32)
+        self._check(self.lib.stn_get_program(self.ctx, _ptr(ops), _ptr(pairs)))
+        return ops, pairs[: self.n_pairs]
+
+    def begin_batch(self, shots, shot_offset=0):
+        self._check(self.lib.stn_begin_batch(self.ctx, int(shots), int(shot_offset)))
+        self.shots = int(shots)
+
+    def apply_round(self, r, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        assert theta.shape == (self.n_pairs,)
+        self._check(self.lib.stn_apply_round(self.ctx, int(r), _ptr(theta)))
+
+    def apply_round_device(self, r, d_theta_ptr):
+        self._check(self.lib.stn_apply_round_device(self.ctx, int(r), ctypes.c_void_p(d_theta_ptr)))
+
+    def sync(self):
+        self._check(self.lib.stn_sync(self.ctx))
+
+    def read_records(self, born=True, stats=True):
+        rec = np.zeros((self.shots, self.rec_bytes), dtype=np.uint8)
+        b = np.zeros((self.shots, self.n_meas), dtype=np.float64) if born else None
+        s = (ShotStats * self.shots)() if stats else None
+        self._check(self.lib.stn_read_records(self.ctx, _ptr(rec), _ptr(b),
+                                              ctypes.cast(s, ctypes.c_void_p) if stats else None))
+        out = {"records": rec, "bits": unpack_records(rec, self.n_meas)}
+        if born:
+            out["born"] = b
+        if stats:
+            out["max_chi"] = np.array([x.max_chi for x in s])
+            out["near_draws"] = np.array([x.near_draws for x in s])
+            out["discarded"] = np.array([x.discarded for x in s])
+            out["logp"] = np.array([x.logp for x in s])
+        return out
+
+    def device_records_ptr(self):
+        return self.lib.stn_device_records(self.ctx)
+
+    def read_tableau(self, shot):
+        rows = 2 * self.n_qubits
+        x = np.zeros((rows, self.words), dtype=np.uint64)
+        z = np.zeros((rows, self.words), dtype=np.uint64)
+        m = np.zeros(rows, dtype=np.uint8)
+        self._check(self.lib.stn_read_tableau(self.ctx, int(shot), _ptr(x), _ptr(z), _ptr(m)))
+        return x, z, m
+
+    def read_bonds(self, shot):
+        b = np.zeros(self.n_qubits - 1, dtype=np.int32)
+        self._check(self.lib.stn_read_bonds(self.ctx, int(shot), _ptr(b)))
+        return b
+
+    def sample_shots(self, shots, shot_offset, theta, born=True, stats=True):
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        self.begin_batch(shots, shot_offset)
+        for r in range(self.rounds + 1):
+            self.apply_round(r, theta)
+        return self.read_records(born=born, stats=stats)
+
+    def logprob_grad(self, records, theta):
+        rec = np.ascontiguousarray(records, dtype=np.uint8)
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        logp = np.zeros(len(rec), dtype=np.float64)
+        grad = np.zeros(self.n_pairs, dtype=np.float64)
+        self._check(self.lib.stn_logprob_grad(self.ctx, _ptr(rec), len(rec), _ptr(theta), _ptr(logp),
+                                              _ptr(grad)))
+        return logp, grad
+
+
+def compile_program(workload):
+    """Host-only compile of the op program (no GPU): (counts, ops[N,6], pairs[K,4])."""
+    lib = load()
+    cfg = config_from_workload(workload)
+    counts = np.zeros(5, dtype=np.int32)
+    st = lib.stn_compile_program(ctypes.byref(cfg), _ptr(counts), None, None)
+    if st != STN_OK:
+        raise StnError(st, "stn_compile_program failed")
+    ops = np.zeros((counts[4], 6), dtype=np.int32)
+    pairs = np.zeros((max(counts[1], 1), 4), dtype=np.int32)
+    st = lib.stn_compile_program(ctypes.byref(cfg), _ptr(counts), _ptr(ops), _ptr(pairs))
+    if st != STN_OK:
+        raise StnError(st, "stn_compile_program failed")
+    return counts, ops, pairs[: counts[1]]
+
+
+def unpack_records(rec, n_meas):
+    bits = np.unpackbits(rec, axis=1, bitorder="little")
+    return bits[:, :n_meas].astype(np.uint8)
+
+
+def philox_uniforms(seed, shot_offset, n_shots, event_offset, n_events, d_out_ptr, stream=0):
+    st = load().stn_philox_uniforms(int(seed), int(shot_offset), int(n_shots), int(event_offset),
+                                    int(n_events), ctypes.c_void_p(d_out_ptr), ctypes.c_void_p(stream))
+    if st != STN_OK:
+        raise StnError(st, "stn_philox_uniforms failed")
+
+
+__all__ = ["Simulator", "StnError", "build", "load", "philox_uniforms", "unpack_records",
+           "config_from_workload", "compile_program"]

@@ -1,0 +1,408 @@
+// C ABI of the simulator (declared in include/stn.h): context, device memory
+// plan, batch control and result readback.  All launches go to the stream the
+// context was created with.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/stn.h"
+#include "engine.h"
+#include "program.h"
+
+struct stn_ctx {
+  stn_config cfg{};
+  stn::Program prog;
+  cudaStream_t stream = nullptr;
+  int64_t max_shots = 0, shots = 0;
+  uint64_t shot_offset = 0;
+  int n = 0, W = 0, rec_bytes = 0, K = 0, grid = 1;
+  std::vector<int> chimax;
+  std::vector<int64_t> site_off;
+  int64_t slab_elems = 0;
+  size_t elem = 8;
+  stn::ScratchPlan plan{};
+  // device memory
+  stn::Op *d_ops = nullptr;
+  double *d_theta = nullptr;
+  uint64_t *d_tx = nullptr, *d_tz = nullptr;
+  uint8_t *d_tm = nullptr;
+  void *d_mps = nullptr;
+  int64_t *d_site_off = nullptr;
+  int *d_chimax = nullptr;
+  int *d_chi = nullptr, *d_center = nullptr, *d_maxchi = nullptr, *d_near = nullptr,
+      *d_status = nullptr;
+  double *d_logp = nullptr, *d_disc = nullptr, *d_born = nullptr;
+  uint8_t *d_rec = nullptr;
+  void *d_scratch = nullptr;
+  int *d_err = nullptr;
+  std::string last_error;
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+stn_status fail(stn_ctx *c, stn_status st, const std::string &msg) {
+  if (c) c->last_error = msg;
+  return st;
+}
+
+stn_status cuda_fail(stn_ctx *c, cudaError_t e, const char *where) {
+  return fail(c, STN_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <typename P>
+cudaError_t dalloc(stn_ctx *c, P **ptr, size_t bytes) {
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+  if (e == cudaSuccess) {
+    c->allocs.push_back(p);
+    *ptr = static_cast<P *>(p);
+  }
+  return e;
+}
+
+stn::EngineParams params(const stn_ctx *c, int seg, const double *d_theta) {
+  stn::EngineParams p{};
+  p.ops = c->d_ops;
+  p.op_begin = c->prog.seg_begin[seg];
+  p.op_end = c->prog.seg_begin[seg + 1];
+  p.theta = d_theta;
+  p.n = c->n;
+  p.W = c->W;
+  p.n_meas = c->prog.n_meas;
+  p.rec_bytes = c->rec_bytes;
+  p.chi_cap = c->cfg.chi_cap;
+  p.cutoff = c->cfg.svd_cutoff;
+  p.delta = c->cfg.degeneracy_tol;
+  p.p1 = c->cfg.p * c->cfg.p1_scale;
+  p.p2 = c->cfg.p * c->cfg.p2_scale;
+  p.pR = c->cfg.p * c->cfg.pR_scale;
+  p.pM = c->cfg.p * c->cfg.pM_scale;
+  p.seed = c->cfg.seed;
+  p.shot_offset = c->shot_offset;
+  p.shots = static_cast<int>(c->shots);
+  p.tab_x = c->d_tx;
+  p.tab_z = c->d_tz;
+  p.tab_m = c->d_tm;
+  p.mps = c->d_mps;
+  p.site_off = c->d_site_off;
+  p.chimax = c->d_chimax;
+  p.slab_elems = c->slab_elems;
+  p.chi = c->d_chi;
+  p.center = c->d_center;
+  p.logp = c->d_logp;
+  p.disc = c->d_disc;
+  p.maxchi = c->d_maxchi;
+  p.near = c->d_near;
+  p.status = c->d_status;
+  p.records = c->d_rec;
+  p.born = c->d_born;
+  p.scratch = c->d_scratch;
+  p.scratch_elems = c->plan.total;
+  p.ap_elems = c->plan.ap_elems;
+  p.g_elems = c->plan.g_elems;
+  p.work_c = c->plan.work_c;
+  p.err = c->d_err;
+  return p;
+}
+
+std::string validate(const stn_config *cfg) {
+  if (!cfg) return "config is NULL";
+  if (cfg->chi_cap < 1 || cfg->chi_cap > 256) return "chi_cap must be 1..256";
+  if (cfg->precision != STN_PRECISION_C128 && cfg->precision != STN_PRECISION_C64)
+    return "precision must be STN_PRECISION_C128 or STN_PRECISION_C64";
+  const double rates[5] = {cfg->p, cfg->p1_scale, cfg->p2_scale, cfg->pR_scale, cfg->pM_scale};
+  for (double r : rates)
+    if (!(r >= 0.0) || !std::isfinite(r)) return "noise rates must be finite and >= 0";
+  const double probs[4] = {cfg->p * cfg->p1_scale, cfg->p * cfg->p2_scale, cfg->p * cfg->pR_scale,
+                           cfg->p * cfg->pM_scale};
+  for (double r : probs)
+    if (r > 1.0) return "scaled noise probabilities must be <= 1";
+  if (!(cfg->svd_cutoff >= 0.0) || !(cfg->svd_cutoff < 1.0)) return "svd_cutoff must be in [0, 1)";
+  if (!(cfg->degeneracy_tol >= 0.0) || !(cfg->degeneracy_tol < 1.0))
+    return "degeneracy_tol must be in [0, 1)";
+  if (cfg->distance > 9) return "distance must be <= 9";
+  return std::string();
+}
+
+}  // namespace
+
+extern "C" {
+
+stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_stream, stn_ctx **out) {
+  if (!out) return STN_EINVAL;
+  *out = nullptr;
+  std::string why = validate(cfg);
+  if (!why.empty()) return STN_EINVAL;
+  if (max_shots < 1 || max_shots > (1ll << 31)) return STN_EINVAL;
+  stn_ctx *c = new (std::nothrow) stn_ctx();
+  if (!c) return STN_ENOMEM;
+  c->cfg = *cfg;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->max_shots = max_shots;
+  why = stn::build_program(cfg->distance, cfg->rounds, cfg->pair_rule, c->prog);
+  if (!why.empty()) {
+    delete c;
+    return STN_EINVAL;
+  }
+  const int n = c->n = c->prog.n;
+  c->W = (n + 63) / 64;
+  c->rec_bytes = (c->prog.n_meas + 7) / 8;
+  c->K = static_cast<int>(c->prog.pairs.size());
+  c->elem = cfg->precision == STN_PRECISION_C128 ? 16 : 8;
+  // largest bond per cut: the cap, and 2^min(k, n-k) (Schmidt rank bound)
+  c->chimax.assign(n + 1, 1);
+  for (int k = 1; k < n; ++k) {
+    int e = std::min(k, n - k);
+    int64_t v = e >= 30 ? (1ll << 30) : (1ll << e);
+    c->chimax[k] = static_cast<int>(std::min<int64_t>(v, cfg->chi_cap));
+  }
+  c->site_off.assign(n + 1, 0);
+  for (int k = 0; k < n; ++k)
+    c->site_off[k + 1] = c->site_off[k] + 2ll * c->chimax[k] * c->chimax[k + 1];
+  c->slab_elems = c->site_off[n];
+  c->plan = stn::plan_scratch(n, c->chimax.data(), cfg->chi_cap);
+
+  int dev = 0, sms = 1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    delete c;
+    return STN_ECUDA;
+  }
+  c->grid = static_cast<int>(std::min<int64_t>(max_shots, sms));
+
+  const int64_t S = max_shots;
+  const size_t nn = static_cast<size_t>(2 * n);
+  bool ok = true;
+  auto A = [&](cudaError_t r) { ok = ok && r == cudaSuccess; };
+  A(dalloc(c, &c->d_ops, sizeof(stn::Op) * c->prog.ops.size()));
+  A(dalloc(c, &c->d_theta, sizeof(double) * std::max(1, c->K)));
+  A(dalloc(c, &c->d_tx, sizeof(uint64_t) * S * nn * c->W));
+  A(dalloc(c, &c->d_tz, sizeof(uint64_t) * S * nn * c->W));
+  A(dalloc(c, &c->d_tm, S * nn));
+  A(dalloc(c, &c->d_mps, c->elem * S * c->slab_elems));
+  A(dalloc(c, &c->d_site_off, sizeof(int64_t) * (n + 1)));
+  A(dalloc(c, &c->d_chimax, sizeof(int) * (n + 1)));
+  A(dalloc(c, &c->d_chi, sizeof(int) * S * (n + 1)));
+  A(dalloc(c, &c->d_center, sizeof(int) * S));
+  A(dalloc(c, &c->d_maxchi, sizeof(int) * S));
+  A(dalloc(c, &c->d_near, sizeof(int) * S));
+  A(dalloc(c, &c->d_status, sizeof(int) * S));
+  A(dalloc(c, &c->d_logp, sizeof(double) * S));
+  A(dalloc(c, &c->d_disc, sizeof(double) * S));
+  A(dalloc(c, &c->d_born, sizeof(double) * S * c->prog.n_meas));
+  A(dalloc(c, &c->d_rec, static_cast<size_t>(S) * c->rec_bytes));
+  A(dalloc(c, &c->d_scratch, c->elem * static_cast<size_t>(c->grid) * c->plan.total));
+  A(dalloc(c, &c->d_err, sizeof(int)));
+  if (!ok) {
+    stn_destroy(c);
+    cudaGetLastError();
+    return STN_ENOMEM;
+  }
+  e = cudaMemcpyAsync(c->d_ops, c->prog.ops.data(), sizeof(stn::Op) * c->prog.ops.size(),
+                      cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_site_off, c->site_off.data(), sizeof(int64_t) * (n + 1),
+                        cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_chimax, c->chimax.data(), sizeof(int) * (n + 1),
+                        cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    stn_destroy(c);
+    return STN_ECUDA;
+  }
+  *out = c;
+  return STN_OK;
+}
+
+void stn_destroy(stn_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (void *p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+const char *stn_last_error(const stn_ctx *c) { return c ? c->last_error.c_str() : "no context"; }
+
+int32_t stn_num_qubits(const stn_ctx *c) { return c ? c->n : -1; }
+int32_t stn_num_pairs(const stn_ctx *c) { return c ? c->K : -1; }
+int32_t stn_num_meas(const stn_ctx *c) { return c ? c->prog.n_meas : -1; }
+int32_t stn_num_events(const stn_ctx *c) { return c ? c->prog.n_events : -1; }
+int32_t stn_num_ops(const stn_ctx *c) { return c ? static_cast<int32_t>(c->prog.ops.size()) : -1; }
+
+static void dump_program(const stn::Program &prog, int32_t *h_ops, int32_t *h_pairs) {
+  if (h_ops) {
+    for (size_t i = 0; i < prog.ops.size(); ++i) {
+      const stn::Op &o = prog.ops[i];
+      int32_t *r = h_ops + 6 * i;
+      r[0] = o.kind; r[1] = o.a; r[2] = o.b; r[3] = o.pauli; r[4] = o.ev; r[5] = o.idx;
+    }
+  }
+  if (h_pairs) {
+    for (size_t k = 0; k < prog.pairs.size(); ++k) {
+      const stn::Pair &p = prog.pairs[k];
+      int32_t *r = h_pairs + 4 * k;
+      r[0] = p.a; r[1] = p.b; r[2] = p.pauli; r[3] = p.layer_mask;
+    }
+  }
+}
+
+stn_status stn_get_program(const stn_ctx *c, int32_t *h_ops, int32_t *h_pairs) {
+  if (!c) return STN_EINVAL;
+  dump_program(c->prog, h_ops, h_pairs);
+  return STN_OK;
+}
+
+stn_status stn_compile_program(const stn_config *cfg, int32_t *h_counts, int32_t *h_ops,
+                               int32_t *h_pairs) {
+  if (!validate(cfg).empty()) return STN_EINVAL;
+  stn::Program prog;
+  if (!stn::build_program(cfg->distance, cfg->rounds, cfg->pair_rule, prog).empty()) return STN_EINVAL;
+  if (h_counts) {
+    h_counts[0] = prog.n;
+    h_counts[1] = static_cast<int32_t>(prog.pairs.size());
+    h_counts[2] = prog.n_meas;
+    h_counts[3] = prog.n_events;
+    h_counts[4] = static_cast<int32_t>(prog.ops.size());
+  }
+  dump_program(prog, h_ops, h_pairs);
+  return STN_OK;
+}
+
+stn_status stn_begin_batch(stn_ctx *c, int64_t shots, uint64_t shot_offset) {
+  if (!c) return STN_EINVAL;
+  if (shots < 1 || shots > c->max_shots) return fail(c, STN_EINVAL, "shots must be 1..max_shots");
+  c->shots = shots;
+  c->shot_offset = shot_offset;
+  cudaError_t e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stn_begin_batch");
+  stn::EngineParams p = params(c, 0, c->d_theta);
+  e = stn::launch_init(c->cfg.precision, p, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+  return STN_OK;
+}
+
+stn_status stn_apply_round_device(stn_ctx *c, int32_t round, const double *d_theta) {
+  if (!c) return STN_EINVAL;
+  if (c->shots < 1) return fail(c, STN_EINVAL, "no batch: call stn_begin_batch first");
+  if (round < 0 || round > c->cfg.rounds) return fail(c, STN_EINVAL, "round must be 0..rounds");
+  if (!d_theta && c->K > 0) return fail(c, STN_EINVAL, "theta is NULL");
+  stn::EngineParams p = params(c, round, d_theta ? d_theta : c->d_theta);
+  int grid = static_cast<int>(std::min<int64_t>(c->grid, c->shots));
+  cudaError_t e = stn::launch_round(c->cfg.precision, p, grid, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "round kernel");
+  return STN_OK;
+}
+
+stn_status stn_apply_round(stn_ctx *c, int32_t round, const double *h_theta) {
+  if (!c) return STN_EINVAL;
+  if (!h_theta && c->K > 0) return fail(c, STN_EINVAL, "theta is NULL");
+  for (int k = 0; k < c->K; ++k)
+    if (!std::isfinite(h_theta[k])) return fail(c, STN_EINVAL, "theta must be finite");
+  if (c->K > 0) {
+    cudaError_t e = cudaMemcpyAsync(c->d_theta, h_theta, sizeof(double) * c->K,
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "theta copy");
+  }
+  return stn_apply_round_device(c, round, c->d_theta);
+}
+
+stn_status stn_sync(stn_ctx *c) {
+  if (!c) return STN_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+  int err = 0;
+  e = cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "error flag");
+  if (err == STN_ENUMERIC) return fail(c, STN_ENUMERIC, "non-finite or vanishing MPS norm in a shot");
+  if (err == STN_EOVERFLOW) return fail(c, STN_EOVERFLOW, "scratch arena too small for a sweep");
+  if (err != 0) return fail(c, static_cast<stn_status>(err), "device reported an error");
+  return STN_OK;
+}
+
+stn_status stn_read_records(stn_ctx *c, uint8_t *h_records, double *h_born,
+                            stn_shot_stats *h_stats) {
+  stn_status st = stn_sync(c);
+  if (st != STN_OK) return st;
+  cudaError_t e = cudaSuccess;
+  if (h_records)
+    e = cudaMemcpy(h_records, c->d_rec, static_cast<size_t>(c->shots) * c->rec_bytes,
+                   cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && h_born)
+    e = cudaMemcpy(h_born, c->d_born, sizeof(double) * c->shots * c->prog.n_meas,
+                   cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && h_stats) {
+    std::vector<int> mx(c->shots), nr(c->shots);
+    std::vector<double> ds(c->shots), lp(c->shots);
+    e = cudaMemcpy(mx.data(), c->d_maxchi, sizeof(int) * c->shots, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(nr.data(), c->d_near, sizeof(int) * c->shots, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(ds.data(), c->d_disc, sizeof(double) * c->shots, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(lp.data(), c->d_logp, sizeof(double) * c->shots, cudaMemcpyDeviceToHost);
+    for (int64_t s = 0; s < c->shots && e == cudaSuccess; ++s)
+      h_stats[s] = stn_shot_stats{mx[s], nr[s], ds[s], lp[s]};
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "stn_read_records");
+  return STN_OK;
+}
+
+const uint8_t *stn_device_records(const stn_ctx *c) { return c ? c->d_rec : nullptr; }
+
+stn_status stn_read_tableau(stn_ctx *c, int64_t shot, uint64_t *h_x, uint64_t *h_z,
+                            uint8_t *h_phase) {
+  if (!c || shot < 0 || shot >= c->shots) return fail(c, STN_EINVAL, "shot out of range");
+  stn_status st = stn_sync(c);
+  if (st != STN_OK) return st;
+  const size_t rows = 2 * c->n, words = rows * c->W;
+  cudaError_t e = cudaSuccess;
+  if (h_x) e = cudaMemcpy(h_x, c->d_tx + shot * words, sizeof(uint64_t) * words, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && h_z)
+    e = cudaMemcpy(h_z, c->d_tz + shot * words, sizeof(uint64_t) * words, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && h_phase)
+    e = cudaMemcpy(h_phase, c->d_tm + shot * rows, rows, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stn_read_tableau");
+  return STN_OK;
+}
+
+stn_status stn_read_bonds(stn_ctx *c, int64_t shot, int32_t *h_bonds) {
+  if (!c || shot < 0 || shot >= c->shots || !h_bonds) return fail(c, STN_EINVAL, "bad argument");
+  stn_status st = stn_sync(c);
+  if (st != STN_OK) return st;
+  std::vector<int> chi(c->n + 1);
+  cudaError_t e = cudaMemcpy(chi.data(), c->d_chi + shot * (c->n + 1), sizeof(int) * (c->n + 1),
+                             cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stn_read_bonds");
+  for (int k = 0; k + 1 < c->n; ++k) h_bonds[k] = chi[k + 1];
+  return STN_OK;
+}
+
+stn_status stn_sample_shots(stn_ctx *c, int64_t shots, uint64_t shot_offset, const double *h_theta,
+                            uint8_t *h_records, double *h_born, stn_shot_stats *h_stats) {
+  stn_status st = stn_begin_batch(c, shots, shot_offset);
+  for (int r = 0; st == STN_OK && r <= c->cfg.rounds; ++r) st = stn_apply_round(c, r, h_theta);
+  if (st != STN_OK) return st;
+  return stn_read_records(c, h_records, h_born, h_stats);
+}
+
+stn_status stn_logprob_grad(stn_ctx *c, const uint8_t *, int64_t, const double *, double *,
+                            double *) {
+  return fail(c, STN_ENOTIMPL, "stn_logprob_grad is not implemented");
+}
+
+stn_status stn_philox_uniforms(uint64_t seed, uint64_t shot_offset, int64_t n_shots,
+                               uint32_t event_offset, int32_t n_events, double *d_out,
+                               void *cuda_stream) {
+  if (n_shots < 0 || n_events < 0 || (!d_out && n_shots * n_events > 0)) return STN_EINVAL;
+  cudaError_t e = stn::launch_philox(seed, shot_offset, n_shots, event_offset, n_events, d_out,
+                                     static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? STN_OK : STN_ECUDA;
+}
+
+}  // extern "C"

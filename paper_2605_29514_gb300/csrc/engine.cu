@@ -1,0 +1,1137 @@
+// Kernels of the stabilizer-tensor-network simulation (sm_103a).
+//
+// One persistent CTA per shot slot walks the op list of a program segment
+// (one syndrome round).  Clifford gates and Pauli noise update the inverse
+// tableau held in shared memory (bit-exact integer row operations, Sec. IV A).
+// A crosstalk rotation or a measurement pushes its Pauli through the tableau
+// and acts on the shot's MPS as a bond-2 Pauli-string MPO; the MPS is then
+// recompressed (Sec. IV B, Eq. 8) by a Gram-matrix sweep:
+//   left sweep   G_{k+1} = sum_s A'^s_k^dag G_k A'^s_k      (left Gram of the
+//                doubled state, G_a = identity since sites < a are
+//                left-canonical)
+//   right sweep  H = M_k^dag G_k M_k, H = V diag(lambda) V^dag; the kept
+//                columns of V give the new right-canonical site, and
+//                M_{k-1} = A'_{k-1} (M_k V) carries the rest to the left.
+// The eigenvalues of H are the squared Schmidt values of the bond, so keeping
+// the largest ones is the truncation of Eq. 8.  Dense work runs in complex
+// T (float or double); norms, Born probabilities and log-probabilities in
+// double.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "../../include/stn.h"
+#include "engine.h"
+
+namespace stn {
+
+// ---------------------------------------------------------------------------
+// complex arithmetic
+template <typename T>
+struct cplx {
+  T re, im;
+};
+template <typename T>
+__device__ __forceinline__ cplx<T> cmake(T r, T i) {
+  cplx<T> c;
+  c.re = r;
+  c.im = i;
+  return c;
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) {
+  return cmake<T>(a.re + b.re, a.im + b.im);
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return cmake<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cconj(cplx<T> a) {
+  return cmake<T>(a.re, -a.im);
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) {
+  return cmake<T>(a.re * s, a.im * s);
+}
+// acc += a * b
+template <typename T>
+__device__ __forceinline__ void cfma(cplx<T> &acc, cplx<T> a, cplx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+template <typename T>
+__device__ __forceinline__ T cabs2(cplx<T> a) {
+  return a.re * a.re + a.im * a.im;
+}
+// i^m
+template <typename T>
+__device__ __forceinline__ cplx<T> ipow(int m) {
+  m &= 3;
+  return m == 0 ? cmake<T>(1, 0) : m == 1 ? cmake<T>(0, 1) : m == 2 ? cmake<T>(-1, 0) : cmake<T>(0, -1);
+}
+
+template <typename T>
+struct Eps;
+template <>
+struct Eps<float> {
+  static constexpr float v = 5.96e-8f;
+};
+template <>
+struct Eps<double> {
+  static constexpr double v = 1.11e-16;
+};
+
+// Matrices that fit this size are diagonalised in shared memory.
+template <typename T>
+struct JacobiSmem;
+template <>
+struct JacobiSmem<float> {
+  static constexpr int n = 80;
+};
+template <>
+struct JacobiSmem<double> {
+  static constexpr int n = 48;
+};
+
+constexpr int kBM = 64, kBN = 64, kBK = 16, kPad = 4;
+constexpr int kMaxPairs = 256;  // Jacobi pairs per round: n <= 512
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): two 32x32->64-bit
+// multiplies per round, Weyl key schedule, ten rounds.
+__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t shot, uint32_t ev) {
+  uint32_t c0 = static_cast<uint32_t>(shot), c1 = static_cast<uint32_t>(shot >> 32);
+  uint32_t c2 = ev, c3 = 0u;
+  uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  uint64_t bits = (static_cast<uint64_t>(c0) << 21) ^ static_cast<uint64_t>(c1 >> 11);
+  return static_cast<double>(bits) * 0x1.0p-53;
+}
+
+__global__ void philox_kernel(uint64_t seed, uint64_t shot_offset, int64_t n_shots,
+                              uint32_t event_offset, int n_events, double *out) {
+  int64_t total = n_shots * static_cast<int64_t>(n_events);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int64_t s = i / n_events;
+    uint32_t e = static_cast<uint32_t>(i % n_events);
+    out[i] = philox_uniform(seed, shot_offset + static_cast<uint64_t>(s), event_offset + e);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CTA-wide helpers
+__device__ __forceinline__ int tid() { return threadIdx.x; }
+
+// Sum of one double per thread over the CTA (red: kThreads doubles of smem).
+__device__ double block_sum(double v, double *red) {
+  red[tid()] = v;
+  __syncthreads();
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if (tid() < s) red[tid()] += red[tid() + s];
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// C = alpha * op(A) op(B) + beta * C, all row-major, op = identity (0) or
+// conjugate transpose (1).  op(A) is M x K, op(B) is K x N.
+template <typename T, int TA, int TB>
+__device__ void cgemm(int M, int N, int K, cplx<T> alpha, const cplx<T> *A, int lda,
+                      const cplx<T> *B, int ldb, cplx<T> beta, cplx<T> *C, int ldc,
+                      cplx<T> *tile) {
+  cplx<T> *As = tile;                    // [kBK][kBM + kPad]
+  cplx<T> *Bs = tile + kBK * (kBM + kPad);  // [kBK][kBN + kPad]
+  const int ty = tid() / 16, tx = tid() % 16;
+  const int tilesM = (M + kBM - 1) / kBM, tilesN = (N + kBN - 1) / kBN;
+  for (int t = 0; t < tilesM * tilesN; ++t) {
+    const int i0 = (t / tilesN) * kBM, j0 = (t % tilesN) * kBN;
+    cplx<T> acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = cmake<T>(0, 0);
+    for (int k0 = 0; k0 < K; k0 += kBK) {
+      // A tile: element (i, k) of op(A)
+#pragma unroll
+      for (int r = 0; r < (kBM * kBK) / kThreads; ++r) {
+        int e = tid() + r * kThreads;
+        int i, k;
+        if (TA == 0) { k = e % kBK; i = e / kBK; } else { i = e % kBM; k = e / kBM; }
+        int gi = i0 + i, gk = k0 + k;
+        cplx<T> v = cmake<T>(0, 0);
+        if (gi < M && gk < K) v = TA == 0 ? A[static_cast<int64_t>(gi) * lda + gk]
+                                          : cconj(A[static_cast<int64_t>(gk) * lda + gi]);
+        As[k * (kBM + kPad) + i] = v;
+      }
+#pragma unroll
+      for (int r = 0; r < (kBN * kBK) / kThreads; ++r) {
+        int e = tid() + r * kThreads;
+        int j, k;
+        if (TB == 0) { j = e % kBN; k = e / kBN; } else { k = e % kBK; j = e / kBK; }
+        int gj = j0 + j, gk = k0 + k;
+        cplx<T> v = cmake<T>(0, 0);
+        if (gj < N && gk < K) v = TB == 0 ? B[static_cast<int64_t>(gk) * ldb + gj]
+                                          : cconj(B[static_cast<int64_t>(gj) * ldb + gk]);
+        Bs[k * (kBN + kPad) + j] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < kBK; ++k) {
+        cplx<T> av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = As[k * (kBM + kPad) + ty + 16 * a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Bs[k * (kBN + kPad) + tx + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) cfma(acc[a][b], av[a], bv[b]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      int gi = i0 + ty + 16 * a;
+      if (gi >= M) continue;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        int gj = j0 + tx + 16 * b;
+        if (gj >= N) continue;
+        cplx<T> *c = &C[static_cast<int64_t>(gi) * ldc + gj];
+        cplx<T> v = cmul(alpha, acc[a][b]);
+        if (beta.re != T(0) || beta.im != T(0)) v = cadd(v, cmul(beta, *c));
+        *c = v;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+struct RotParam {
+  int p, q, skip;
+  T cs, sn, shift;  // shift = t |c|
+  cplx<T> u;        // phase of A[p][q]
+};
+
+// Hermitian eigendecomposition A = V diag(lambda) V^dag by cyclic Jacobi with
+// the round-robin parallel ordering (n/2 disjoint rotations per step).  A is
+// overwritten (it becomes diagonal).  A and V may live in shared or global
+// memory.
+template <typename T>
+__device__ void jacobi_heev(int n, cplx<T> *A, int lda, cplx<T> *V, int ldv, RotParam<T> *rp,
+                            int *flag, double *red) {
+  double tr = 0;
+  for (int e = tid(); e < n * n; e += kThreads) {
+    int i = e / n, j = e % n;
+    V[i * ldv + j] = cmake<T>(i == j ? T(1) : T(0), 0);
+    if (i == j) tr += fabs(static_cast<double>(A[i * lda + i].re));
+  }
+  tr = block_sum(tr, red);
+  if (n == 1) return;
+  const int m = n + (n & 1);
+  const int half = m / 2;
+  const T eps = Eps<T>::v;
+  // rotations below this size are skipped: they move eigenvalues by less
+  // than eps * trace
+  const T floor_abs = static_cast<T>(1e-3 * static_cast<double>(eps) * tr);
+  const int max_sweeps = sizeof(T) == 4 ? 15 : 20;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid() == 0) *flag = 0;
+    __syncthreads();
+    for (int round = 0; round < m - 1; ++round) {
+      for (int pi = tid(); pi < half; pi += kThreads) {
+        int p, q;
+        if (pi == 0) { p = m - 1; q = round; }
+        else { p = (round + pi) % (m - 1); q = (round - pi + (m - 1)) % (m - 1); }
+        if (p > q) { int t = p; p = q; q = t; }
+        RotParam<T> r;
+        r.p = p; r.q = q; r.skip = 1; r.cs = 1; r.sn = 0; r.shift = 0; r.u = cmake<T>(1, 0);
+        if (q < n) {
+          T a = A[p * lda + p].re, b = A[q * lda + q].re;
+          cplx<T> c = A[p * lda + q];
+          T absc = sqrt(cabs2(c));
+          T scale = fabs(a) + fabs(b);
+          if (absc > eps * scale * T(0.5) && absc > floor_abs) {
+            T zeta = (b - a) / (T(2) * absc);
+            T t = (zeta >= 0 ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+            r.cs = T(1) / sqrt(T(1) + t * t);
+            r.sn = t * r.cs;
+            r.shift = t * absc;
+            r.u = cmake<T>(c.re / absc, c.im / absc);
+            r.skip = 0;
+            *flag = 1;
+          }
+        }
+        rp[pi] = r;
+      }
+      __syncthreads();
+      // rows: A <- J^dag A; row p' = cs row_p - sn u row_q, row q' = sn row_p + cs u row_q
+      for (int e = tid(); e < half * n; e += kThreads) {
+        const RotParam<T> &r = rp[e / n];
+        if (r.skip) continue;
+        int j = e % n;
+        cplx<T> ap = A[r.p * lda + j], aq = A[r.q * lda + j];
+        cplx<T> uaq = cmul(r.u, aq);
+        A[r.p * lda + j] = cmake<T>(r.cs * ap.re - r.sn * uaq.re, r.cs * ap.im - r.sn * uaq.im);
+        A[r.q * lda + j] = cmake<T>(r.sn * ap.re + r.cs * uaq.re, r.sn * ap.im + r.cs * uaq.im);
+      }
+      __syncthreads();
+      // columns of A and V: col p' = cs col_p - sn conj(u) col_q, col q' = sn col_p + cs conj(u) col_q
+      for (int e = tid(); e < half * n; e += kThreads) {
+        const RotParam<T> &r = rp[e / n];
+        if (r.skip) continue;
+        int i = e % n;
+        cplx<T> uc = cconj(r.u);
+        cplx<T> ap = A[i * lda + r.p], aq = cmul(uc, A[i * lda + r.q]);
+        A[i * lda + r.p] = cmake<T>(r.cs * ap.re - r.sn * aq.re, r.cs * ap.im - r.sn * aq.im);
+        A[i * lda + r.q] = cmake<T>(r.sn * ap.re + r.cs * aq.re, r.sn * ap.im + r.cs * aq.im);
+        cplx<T> vp = V[i * ldv + r.p], vq = cmul(uc, V[i * ldv + r.q]);
+        V[i * ldv + r.p] = cmake<T>(r.cs * vp.re - r.sn * vq.re, r.cs * vp.im - r.sn * vq.im);
+        V[i * ldv + r.q] = cmake<T>(r.sn * vp.re + r.cs * vq.re, r.sn * vp.im + r.cs * vq.im);
+      }
+      __syncthreads();
+      for (int pi = tid(); pi < half; pi += kThreads) {
+        const RotParam<T> &r = rp[pi];
+        if (r.skip) continue;
+        // the 2x2 pivot block is diagonal in exact arithmetic
+        A[r.p * lda + r.q] = cmake<T>(0, 0);
+        A[r.q * lda + r.p] = cmake<T>(0, 0);
+      }
+      __syncthreads();
+    }
+    int f = *flag;
+    __syncthreads();
+    if (!f) break;
+  }
+}
+
+// Descending order of lambda (ties by index): perm[rank] = index.
+template <typename T>
+__device__ void sort_desc(int n, const T *lam, int *perm) {
+  for (int i = tid(); i < n; i += kThreads) perm[i] = i;
+  __syncthreads();
+  for (int i = tid(); i < n; i += kThreads) {
+    T li = lam[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      T lj = lam[j];
+      rank += (lj > li) || (lj == li && j < i);
+    }
+    if (li == li && rank < n) perm[rank] = i;  // a NaN keeps the identity slot
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// The MPO of one rotation or measurement.
+enum MpoKind { MPO_ROT = 0, MPO_PROJ_Z = 1, MPO_PROJ_B = 2 };
+
+template <typename T>
+struct MpoSpec {
+  int kind, lo, hi, j;
+  cplx<T> w0, w1;  // branch weights (folded into site lo)
+  cplx<T> v0, v1;  // measurement eigenvector at site j (case B)
+};
+
+// 2x2 operator (row-major op[s*2 + t]) of branch `br` at site k of the span.
+template <typename T>
+__device__ void site_op(const MpoSpec<T> &sp, const uint64_t *ppx, const uint64_t *ppz, int k,
+                        int br, cplx<T> op[4]) {
+  const bool x = (ppx[k >> 6] >> (k & 63)) & 1, z = (ppz[k >> 6] >> (k & 63)) & 1;
+  const cplx<T> zero = cmake<T>(0, 0), one = cmake<T>(1, 0);
+  op[0] = one; op[1] = zero; op[2] = zero; op[3] = one;
+  if (br == 1) {
+    if (sp.kind == MPO_PROJ_B && k == sp.j) {
+      op[0] = zero; op[1] = cconj(sp.v1); op[2] = zero; op[3] = zero;
+    } else if (sp.kind == MPO_PROJ_B) {
+      // Hermitian letter of P' at k (controlled-Pauli target)
+      if (x && !z) { op[0] = zero; op[1] = one; op[2] = one; op[3] = zero; }
+      else if (x && z) { op[0] = zero; op[1] = cmake<T>(0, -1); op[2] = cmake<T>(0, 1); op[3] = zero; }
+      else if (z) { op[3] = cmake<T>(-1, 0); }
+    } else {
+      // X^x Z^z (MPO_PROJ_Z has x = 0 on every site)
+      if (x && !z) { op[0] = zero; op[1] = one; op[2] = one; op[3] = zero; }
+      else if (x && z) { op[0] = zero; op[1] = cmake<T>(-1, 0); op[2] = one; op[3] = zero; }
+      else if (z) { op[3] = cmake<T>(-1, 0); }
+    }
+  } else if (sp.kind == MPO_PROJ_B && k == sp.j) {
+    op[0] = cconj(sp.v0); op[3] = zero;
+  }
+  if (k == sp.lo) {
+    cplx<T> w = br == 0 ? sp.w0 : sp.w1;
+    for (int i = 0; i < 4; ++i) op[i] = cmul(w, op[i]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory layout of the round kernel.
+template <typename T>
+struct Smem {
+  uint64_t *tx, *tz, *ppx, *ppz;
+  uint8_t *tm;
+  int *chi, *perm, *misc;
+  int64_t *off;  // span offsets: Ap stack [n+2], G stack [n+2]
+  int64_t *goff;
+  double *red;
+  double *dmisc;
+  cplx<T> *tile;
+  RotParam<T> *rp;
+  cplx<T> *jA, *jV;
+  T *lam;
+  MpoSpec<T> *spec;
+};
+
+template <typename T>
+__host__ __device__ size_t smem_bytes(int n, int W) {
+  const int NS = JacobiSmem<T>::n;
+  size_t b = 0;
+  auto add = [&](size_t bytes) { b += (bytes + 15) & ~size_t(15); };
+  add(sizeof(uint64_t) * 2 * n * W);  // tx
+  add(sizeof(uint64_t) * 2 * n * W);  // tz
+  add(sizeof(uint64_t) * W);          // ppx
+  add(sizeof(uint64_t) * W);          // ppz
+  add(2 * n);                         // tm
+  add(sizeof(int) * (n + 2));         // chi
+  add(sizeof(int) * 512);             // perm
+  add(sizeof(int) * 16);              // misc
+  add(sizeof(int64_t) * (n + 2));     // off
+  add(sizeof(int64_t) * (n + 2));     // goff
+  add(sizeof(double) * kThreads);     // red
+  add(sizeof(double) * 8);            // dmisc
+  add(sizeof(cplx<T>) * kBK * (kBM + kPad + kBN + kPad));  // tile
+  add(sizeof(RotParam<T>) * kMaxPairs);
+  add(sizeof(cplx<T>) * NS * NS);     // jA
+  add(sizeof(cplx<T>) * NS * NS);     // jV
+  add(sizeof(T) * 512);               // lam
+  add(sizeof(MpoSpec<T>));
+  return b;
+}
+
+template <typename T>
+__device__ Smem<T> carve(char *base, int n, int W) {
+  const int NS = JacobiSmem<T>::n;
+  Smem<T> s;
+  size_t b = 0;
+  auto take = [&](size_t bytes) {
+    char *p = base + b;
+    b += (bytes + 15) & ~size_t(15);
+    return p;
+  };
+  s.tx = reinterpret_cast<uint64_t *>(take(sizeof(uint64_t) * 2 * n * W));
+  s.tz = reinterpret_cast<uint64_t *>(take(sizeof(uint64_t) * 2 * n * W));
+  s.ppx = reinterpret_cast<uint64_t *>(take(sizeof(uint64_t) * W));
+  s.ppz = reinterpret_cast<uint64_t *>(take(sizeof(uint64_t) * W));
+  s.tm = reinterpret_cast<uint8_t *>(take(2 * n));
+  s.chi = reinterpret_cast<int *>(take(sizeof(int) * (n + 2)));
+  s.perm = reinterpret_cast<int *>(take(sizeof(int) * 512));
+  s.misc = reinterpret_cast<int *>(take(sizeof(int) * 16));
+  s.off = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (n + 2)));
+  s.goff = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (n + 2)));
+  s.red = reinterpret_cast<double *>(take(sizeof(double) * kThreads));
+  s.dmisc = reinterpret_cast<double *>(take(sizeof(double) * 8));
+  s.tile = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * kBK * (kBM + kPad + kBN + kPad)));
+  s.rp = reinterpret_cast<RotParam<T> *>(take(sizeof(RotParam<T>) * kMaxPairs));
+  s.jA = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * NS * NS));
+  s.jV = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * NS * NS));
+  s.lam = reinterpret_cast<T *>(take(sizeof(T) * 512));
+  s.spec = reinterpret_cast<MpoSpec<T> *>(take(sizeof(MpoSpec<T>)));
+  return s;
+}
+
+// misc slots
+enum { M_LO = 0, M_HI, M_A, M_B, M_CENTER, M_FAIL, M_JFLAG, M_KEEP, M_MAXCHI, M_CASEB, M_J, M_BIT, M_LIDX, M_OUTCOME };
+// dmisc slots
+enum { D_DISC = 0, D_LOGP, D_E, D_NORM };
+
+// Per-CTA scratch partition (complex elements).
+template <typename T>
+struct Scratch {
+  cplx<T> *ap, *g, *t, *y, *h, *v, *vs, *w, *mbuf, *e, *sa, *te;
+  T *lam;
+};
+
+template <typename T>
+__device__ Scratch<T> scratch_for(const EngineParams &P, int cap) {
+  Scratch<T> s;
+  cplx<T> *base = reinterpret_cast<cplx<T> *>(P.scratch) + static_cast<int64_t>(blockIdx.x) * P.scratch_elems;
+  const int64_t c2 = static_cast<int64_t>(cap) * cap;
+  s.ap = base;
+  s.g = s.ap + P.ap_elems;
+  s.t = s.g + P.g_elems;
+  s.y = s.t + 8 * c2;
+  s.h = s.y + 4 * c2;
+  s.v = s.h + 4 * c2;
+  s.vs = s.v + 4 * c2;
+  s.w = s.vs + 4 * c2;
+  s.mbuf = s.w + 2 * c2;
+  s.e = s.mbuf + 4 * c2;
+  s.sa = s.e + c2;
+  s.te = s.sa + 2 * c2;
+  s.lam = reinterpret_cast<T *>(s.te + 2 * c2);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// MPS pieces (CTA-wide).
+template <typename T>
+__device__ __forceinline__ cplx<T> *site_ptr(const EngineParams &P, int64_t shot, int k) {
+  return reinterpret_cast<cplx<T> *>(P.mps) + shot * P.slab_elems + P.site_off[k];
+}
+
+// out = branch-summed MPO tensor of site k (see header comment): left bond
+// doubled when dl, right bond doubled when dr; the (alpha, l) index is
+// alpha * chl + l.
+template <typename T>
+__device__ void materialize(const MpoSpec<T> &sp, const uint64_t *ppx, const uint64_t *ppz, int k,
+                            const cplx<T> *A, int chl, int chr, bool dl, bool dr, cplx<T> *out) {
+  cplx<T> op0[4], op1[4];
+  site_op(sp, ppx, ppz, k, 0, op0);
+  site_op(sp, ppx, ppz, k, 1, op1);
+  const int Dl = dl ? 2 * chl : chl, Dr = dr ? 2 * chr : chr;
+  const int64_t total = static_cast<int64_t>(Dl) * 2 * Dr;
+  for (int64_t e = tid(); e < total; e += kThreads) {
+    int R = static_cast<int>(e % Dr);
+    int s = static_cast<int>((e / Dr) % 2);
+    int L = static_cast<int>(e / (2 * Dr));
+    int al = dl ? L / chl : -1, l = dl ? L % chl : L;
+    int be = dr ? R / chr : -1, r = dr ? R % chr : R;
+    cplx<T> val = cmake<T>(0, 0);
+    if (!(dl && dr && al != be)) {
+      int br = dl ? al : be;
+      cplx<T> a0 = A[(static_cast<int64_t>(l) * 2 + 0) * chr + r];
+      cplx<T> a1 = A[(static_cast<int64_t>(l) * 2 + 1) * chr + r];
+      if (br < 0) {
+        cfma(val, cadd(op0[s * 2 + 0], op1[s * 2 + 0]), a0);
+        cfma(val, cadd(op0[s * 2 + 1], op1[s * 2 + 1]), a1);
+      } else {
+        const cplx<T> *op = br == 0 ? op0 : op1;
+        cfma(val, op[s * 2 + 0], a0);
+        cfma(val, op[s * 2 + 1], a1);
+      }
+    }
+    out[e] = val;
+  }
+}
+
+// Keep count at one bond from eigenvalues sorted in decreasing order.
+template <typename T>
+__device__ int keep_count(const T *lam_sorted, int n, int cap, double cutoff, double delta) {
+  double s1 = sqrt(fmax(static_cast<double>(lam_sorted[0]), 0.0));
+  if (!(s1 > 0.0)) return 1;
+  int k = 0;
+  for (int i = 0; i < n; ++i)
+    if (sqrt(fmax(static_cast<double>(lam_sorted[i]), 0.0)) > cutoff * s1) ++k;
+  if (k < 1) k = 1;
+  if (k > cap) {
+    double thr = sqrt(fmax(static_cast<double>(lam_sorted[cap]), 0.0)) + delta * s1;
+    int kk = 0;
+    for (int i = 0; i < cap; ++i)
+      if (sqrt(fmax(static_cast<double>(lam_sorted[i]), 0.0)) > thr) ++kk;
+    k = kk < 1 ? 1 : kk;
+  }
+  return k;
+}
+
+// Apply the two-branch MPO `spec` on [lo, hi] and recompress sites [a, b]
+// (a <= lo <= hi <= b, the orthogonality centre inside [a, b]).  The centre
+// ends at a and the state is renormalised.
+template <typename T>
+__device__ void mps_apply_compress(const EngineParams &P, const Smem<T> &S, int64_t shot,
+                                   const Scratch<T> &X, int a, int b) {
+  const MpoSpec<T> &sp = *S.spec;
+  int *chi = S.chi;
+  const int cap = P.chi_cap;
+  if (a == b) {
+    cplx<T> *A = site_ptr<T>(P, shot, a);
+    materialize(sp, S.ppx, S.ppz, a, A, chi[a], chi[a + 1], false, false, X.t);
+    __syncthreads();
+    const int64_t tot = static_cast<int64_t>(chi[a]) * 2 * chi[a + 1];
+    double nrm = 0;
+    for (int64_t e = tid(); e < tot; e += kThreads) nrm += static_cast<double>(cabs2(X.t[e]));
+    nrm = block_sum(nrm, S.red);
+    T inv = static_cast<T>(nrm > 0 ? 1.0 / sqrt(nrm) : 0.0);
+    for (int64_t e = tid(); e < tot; e += kThreads) A[e] = cscale(X.t[e], inv);
+    if (tid() == 0) {
+      if (!(nrm > 0) || !isfinite(nrm)) S.misc[M_FAIL] = STN_ENUMERIC;
+      S.misc[M_CENTER] = a;
+    }
+    __syncthreads();
+    return;
+  }
+  // doubled bond dimensions D[k] for bonds a..b+1
+  auto Dbond = [&](int k) { return (k > sp.lo && k <= sp.hi) ? 2 * chi[k] : chi[k]; };
+  if (tid() == 0) {
+    int64_t o = 0;
+    for (int k = a; k <= b; ++k) {
+      S.off[k - a] = o;
+      o += static_cast<int64_t>(Dbond(k)) * 2 * Dbond(k + 1);
+    }
+    S.off[b - a + 1] = o;
+    int64_t g = 0;
+    for (int k = a + 1; k <= b; ++k) {
+      S.goff[k - a] = g;
+      g += static_cast<int64_t>(Dbond(k)) * Dbond(k);
+    }
+    S.goff[b - a + 1] = g;
+    if (o > P.ap_elems || g > P.g_elems) S.misc[M_FAIL] = STN_EOVERFLOW;
+  }
+  __syncthreads();
+  if (S.misc[M_FAIL]) return;
+  for (int k = a; k <= b; ++k) {
+    bool in = k >= sp.lo && k <= sp.hi;
+    bool dl = in && k > sp.lo, dr = in && k < sp.hi;
+    cplx<T> *A = site_ptr<T>(P, shot, k);
+    cplx<T> *out = X.ap + S.off[k - a];
+    if (in) {
+      materialize(sp, S.ppx, S.ppz, k, A, chi[k], chi[k + 1], dl, dr, out);
+    } else {
+      const int64_t tot = static_cast<int64_t>(chi[k]) * 2 * chi[k + 1];
+      for (int64_t e = tid(); e < tot; e += kThreads) out[e] = A[e];
+    }
+  }
+  __syncthreads();
+  const cplx<T> one = cmake<T>(1, 0), zero = cmake<T>(0, 0);
+  // left sweep: G_{k+1} (bond k+1) for k = a..b-1
+  for (int k = a; k < b; ++k) {
+    const int Dl = Dbond(k), Dr = Dbond(k + 1);
+    const cplx<T> *Ak = X.ap + S.off[k - a];
+    cplx<T> *Gout = X.g + S.goff[k + 1 - a];
+    if (k == a) {
+      cgemm<T, 1, 0>(Dr, Dr, 2 * Dl, one, Ak, Dr, Ak, Dr, zero, Gout, Dr, S.tile);
+    } else {
+      const cplx<T> *Gin = X.g + S.goff[k - a];
+      cgemm<T, 0, 0>(Dl, 2 * Dr, Dl, one, Gin, Dl, Ak, 2 * Dr, zero, X.t, 2 * Dr, S.tile);
+      cgemm<T, 1, 0>(Dr, Dr, 2 * Dl, one, Ak, Dr, X.t, Dr, zero, Gout, Dr, S.tile);
+    }
+  }
+  // right sweep
+  int kappa = Dbond(b + 1);
+  const cplx<T> *M = X.ap + S.off[b - a];
+  double disc = 0.0;
+  for (int k = b; k > a; --k) {
+    const int Dl = Dbond(k);
+    const int n2 = 2 * kappa;
+    const cplx<T> *Gk = X.g + S.goff[k - a];
+    cgemm<T, 0, 0>(Dl, n2, Dl, one, Gk, Dl, M, n2, zero, X.y, n2, S.tile);
+    // H = M^dag Y (n2 x n2)
+    const int NS = JacobiSmem<T>::n;
+    const bool in_smem = n2 <= NS;
+    cplx<T> *H = in_smem ? S.jA : X.h;
+    cplx<T> *V = in_smem ? S.jV : X.v;
+    const int ldh = n2;
+    cgemm<T, 1, 0>(n2, n2, Dl, one, M, n2, X.y, n2, zero, H, ldh, S.tile);
+    if (n2 > 2 * kMaxPairs) {
+      if (tid() == 0) S.misc[M_FAIL] = STN_EOVERFLOW;
+      __syncthreads();
+      return;
+    }
+    jacobi_heev<T>(n2, H, ldh, V, n2, S.rp, &S.misc[M_JFLAG], S.red);
+    for (int i = tid(); i < n2; i += kThreads) {
+      T l = H[i * ldh + i].re;
+      if (!isfinite(static_cast<double>(l))) {
+        S.misc[M_FAIL] = STN_ENUMERIC;
+        l = T(0);
+      }
+      X.lam[i] = l;
+    }
+    __syncthreads();
+    if (S.misc[M_FAIL]) return;
+    sort_desc<T>(n2, X.lam, S.perm);
+    for (int i = tid(); i < n2; i += kThreads) S.lam[i] = X.lam[S.perm[i]];
+    __syncthreads();
+    if (tid() == 0) {
+      int kmax = min(cap, P.chimax[k]);
+      int keep = keep_count<T>(S.lam, n2, kmax, P.cutoff, P.delta);
+      if (keep > kmax) keep = kmax;
+      double tot = 0, drop = 0;
+      for (int i = 0; i < n2; ++i) {
+        double l = fmax(static_cast<double>(S.lam[i]), 0.0);
+        tot += l;
+        if (i >= keep) drop += l;
+      }
+      if (tot > 0) S.dmisc[D_DISC] += drop / tot;
+      S.misc[M_KEEP] = keep;
+    }
+    __syncthreads();
+    const int keep = S.misc[M_KEEP];
+    // sorted, kept eigenvectors: Vs[:, c] = V[:, perm[c]], c < keep
+    for (int e = tid(); e < n2 * keep; e += kThreads) {
+      int i = e / keep, c = e % keep;
+      X.vs[i * keep + c] = V[i * n2 + S.perm[c]];
+    }
+    __syncthreads();
+    // new right-canonical site k: B[c][s][r] = conj(Vs[(s*kappa + r)][c])
+    cplx<T> *Bk = site_ptr<T>(P, shot, k);
+    for (int e = tid(); e < keep * n2; e += kThreads) {
+      int c = e / n2, sr = e % n2;
+      Bk[e] = cconj(X.vs[sr * keep + c]);
+    }
+    // W = M Vs (Dl x keep)
+    cgemm<T, 0, 0>(Dl, keep, n2, one, M, n2, X.vs, keep, zero, X.w, keep, S.tile);
+    // M_{k-1} = A'_{k-1} (left reshape 2D_{k-1} x Dl) W
+    const int Dll = Dbond(k - 1);
+    const cplx<T> *Akm1 = X.ap + S.off[k - 1 - a];
+    cgemm<T, 0, 0>(2 * Dll, keep, Dl, one, Akm1, Dl, X.w, keep, zero, X.mbuf, keep, S.tile);
+    if (tid() == 0) chi[k] = keep;
+    __syncthreads();
+    M = X.mbuf;
+    kappa = keep;
+  }
+  // centre site a = M (chi[a] x 2 x kappa), renormalised
+  cplx<T> *Aa = site_ptr<T>(P, shot, a);
+  const int64_t tot = static_cast<int64_t>(chi[a]) * 2 * kappa;
+  double nrm = 0;
+  for (int64_t e = tid(); e < tot; e += kThreads) nrm += static_cast<double>(cabs2(M[e]));
+  nrm = block_sum(nrm, S.red);
+  T inv = static_cast<T>(nrm > 0 ? 1.0 / sqrt(nrm) : 0.0);
+  for (int64_t e = tid(); e < tot; e += kThreads) Aa[e] = cscale(M[e], inv);
+  if (tid() == 0) {
+    if (!(nrm > 0) || !isfinite(nrm)) S.misc[M_FAIL] = STN_ENUMERIC;
+    S.misc[M_CENTER] = a;
+    int mx = S.misc[M_MAXCHI];
+    for (int k = a + 1; k <= b; ++k) mx = max(mx, chi[k]);
+    S.misc[M_MAXCHI] = mx;
+  }
+  __syncthreads();
+  (void)disc;
+}
+
+// <phi| i^m X^x Z^z |phi> over sites [a, b] (centre inside, so the rest of
+// the chain contracts to the identity).  Returns the real part.
+template <typename T>
+__device__ double mps_expect(const EngineParams &P, const Smem<T> &S, int64_t shot,
+                             const Scratch<T> &X, int a, int b, int m) {
+  const int *chi = S.chi;
+  const cplx<T> one = cmake<T>(1, 0), zero = cmake<T>(0, 0);
+  MpoSpec<T> sp;
+  sp.kind = MPO_ROT; sp.lo = -1; sp.hi = -1; sp.j = -1;
+  sp.w0 = one; sp.w1 = one; sp.v0 = zero; sp.v1 = zero;
+  for (int k = a; k <= b; ++k) {
+    const cplx<T> *A = site_ptr<T>(P, shot, k);
+    const int cl = chi[k], cr = chi[k + 1];
+    // SA = (X^x Z^z)_k A_k
+    cplx<T> op[4];
+    site_op(sp, S.ppx, S.ppz, k, 1, op);
+    const int64_t tot = static_cast<int64_t>(cl) * 2 * cr;
+    for (int64_t e = tid(); e < tot; e += kThreads) {
+      int r = static_cast<int>(e % cr), s = static_cast<int>((e / cr) % 2);
+      int64_t l = e / (2 * cr);
+      cplx<T> v = cmake<T>(0, 0);
+      cfma(v, op[s * 2 + 0], A[(l * 2 + 0) * cr + r]);
+      cfma(v, op[s * 2 + 1], A[(l * 2 + 1) * cr + r]);
+      X.sa[e] = v;
+    }
+    __syncthreads();
+    if (k == a) {
+      cgemm<T, 1, 0>(cr, cr, 2 * cl, one, A, cr, X.sa, cr, zero, X.e, cr, S.tile);
+    } else {
+      cgemm<T, 0, 0>(cl, 2 * cr, cl, one, X.e, cl, X.sa, 2 * cr, zero, X.te, 2 * cr, S.tile);
+      cgemm<T, 1, 0>(cr, cr, 2 * cl, one, A, cr, X.te, cr, zero, X.e, cr, S.tile);
+    }
+  }
+  const int cb = chi[b + 1];
+  double re = 0, im = 0;
+  for (int i = tid(); i < cb; i += kThreads) {
+    re += static_cast<double>(X.e[i * cb + i].re);
+    im += static_cast<double>(X.e[i * cb + i].im);
+  }
+  re = block_sum(re, S.red);
+  im = block_sum(im, S.red);
+  // multiply by i^m, keep the real part
+  switch (m & 3) {
+    case 0: return re;
+    case 1: return -im;
+    case 2: return -re;
+    default: return im;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tableau helpers (shared memory, one thread unless noted).
+__device__ __forceinline__ int popc64(uint64_t v) { return __popcll(v); }
+
+// row r <- row r * row s (Pauli product with the exact phase)
+__device__ void row_mul(uint64_t *tx, uint64_t *tz, uint8_t *tm, int W, int r, int s) {
+  int sw = 0;
+  for (int w = 0; w < W; ++w) {
+    sw += popc64(tz[r * W + w] & tx[s * W + w]);
+    tx[r * W + w] ^= tx[s * W + w];
+    tz[r * W + w] ^= tz[s * W + w];
+  }
+  tm[r] = static_cast<uint8_t>((tm[r] + tm[s] + 2 * sw) & 3);
+}
+
+// rows of X errors anticommute with Z_q, and vice versa
+__device__ void pauli_left(uint8_t *tm, int n, int q, int letter /*1 X, 2 Y, 3 Z*/) {
+  if (letter == 1 || letter == 2) tm[n + q] = static_cast<uint8_t>((tm[n + q] + 2) & 3);
+  if (letter == 3 || letter == 2) tm[q] = static_cast<uint8_t>((tm[q] + 2) & 3);
+}
+
+// P' = row r1 * row r2 (r2 < 0: just row r1) into ppx/ppz, phase returned
+__device__ int conj_rows(const uint64_t *tx, const uint64_t *tz, const uint8_t *tm, int W, int r1,
+                         int r2, uint64_t *ppx, uint64_t *ppz) {
+  int m = tm[r1];
+  int sw = 0;
+  for (int w = 0; w < W; ++w) {
+    ppx[w] = tx[r1 * W + w];
+    ppz[w] = tz[r1 * W + w];
+    if (r2 >= 0) {
+      sw += popc64(ppz[w] & tx[r2 * W + w]);
+      ppx[w] ^= tx[r2 * W + w];
+      ppz[w] ^= tz[r2 * W + w];
+    }
+  }
+  if (r2 >= 0) m += tm[r2] + 2 * sw;
+  return m & 3;
+}
+
+// Single-qubit Clifford L applied to the site-j letter of every row:
+// R -> L R L^dag, for the four L that take the measured eigenvector to |0>:
+// index 0: X,+1 (H)  1: X,-1 (X H)  2: Y,+1 (H S^dag)  3: Y,-1 (X H S^dag).
+// Table: [L][xz] -> (x', z', dm) with xz = 2x + z.
+__constant__ uint8_t kLTable[4][4][3] = {
+    {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {1, 1, 2}},
+    {{0, 0, 0}, {1, 0, 0}, {0, 1, 2}, {1, 1, 0}},
+    {{0, 0, 0}, {1, 0, 0}, {1, 1, 1}, {0, 1, 3}},
+    {{0, 0, 0}, {1, 0, 0}, {1, 1, 3}, {0, 1, 1}},
+};
+
+// C <- C U L^dag for U = prod_{k != j} controlled-P'_k (control j): every row
+// R -> L (U R U) L^dag, with U R U = R Z_j^a (x_j(R) = 0) or
+// (-1)^a R Z_j^a Q (x_j(R) = 1), a = [R anticommutes with Q],
+// Q = prod_{k != j} P'_k.  CTA-wide over rows.
+__device__ void tableau_caseB(uint64_t *tx, uint64_t *tz, uint8_t *tm, int n, int W,
+                              const uint64_t *ppx, const uint64_t *ppz, int j, int lidx) {
+  const int jw = j >> 6;
+  const uint64_t jb = 1ull << (j & 63);
+  for (int r = tid(); r < 2 * n; r += kThreads) {
+    int an = 0, mq = 0;
+    for (int w = 0; w < W; ++w) {
+      uint64_t xq = ppx[w] & (w == jw ? ~jb : ~0ull);
+      uint64_t zq = ppz[w] & (w == jw ? ~jb : ~0ull);
+      an += popc64((tx[r * W + w] & zq) ^ (tz[r * W + w] & xq));
+      mq += popc64(xq & zq);
+    }
+    an &= 1;
+    const bool xj = (tx[r * W + jw] & jb) != 0;
+    int m = tm[r];
+    if (an) tz[r * W + jw] ^= jb;
+    if (xj) {
+      if (an) m += 2;
+      int sw = 0;
+      for (int w = 0; w < W; ++w) {
+        uint64_t xq = ppx[w] & (w == jw ? ~jb : ~0ull);
+        uint64_t zq = ppz[w] & (w == jw ? ~jb : ~0ull);
+        sw += popc64(tz[r * W + w] & xq);
+        tx[r * W + w] ^= xq;
+        tz[r * W + w] ^= zq;
+      }
+      m += mq + 2 * sw;
+    }
+    int x = (tx[r * W + jw] & jb) ? 1 : 0, z = (tz[r * W + jw] & jb) ? 1 : 0;
+    const uint8_t *e = kLTable[lidx][2 * x + z];
+    if (e[0]) tx[r * W + jw] |= jb; else tx[r * W + jw] &= ~jb;
+    if (e[1]) tz[r * W + jw] |= jb; else tz[r * W + jw] &= ~jb;
+    tm[r] = static_cast<uint8_t>((m + e[2]) & 3);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const int n = P.n, W = P.W;
+  Smem<T> S = carve<T>(smem_raw, n, W);
+  Scratch<T> X = scratch_for<T>(P, P.work_c);
+  for (int64_t shot = blockIdx.x; shot < P.shots; shot += gridDim.x) {
+    // load the frame and the MPS bookkeeping
+    for (int e = tid(); e < 2 * n * W; e += kThreads) {
+      S.tx[e] = P.tab_x[shot * 2 * n * W + e];
+      S.tz[e] = P.tab_z[shot * 2 * n * W + e];
+    }
+    for (int e = tid(); e < 2 * n; e += kThreads) S.tm[e] = P.tab_m[shot * 2 * n + e];
+    for (int e = tid(); e <= n; e += kThreads) S.chi[e] = P.chi[shot * (n + 1) + e];
+    if (tid() == 0) {
+      S.misc[M_CENTER] = P.center[shot];
+      S.misc[M_FAIL] = P.status[shot];
+      S.misc[M_MAXCHI] = P.maxchi[shot];
+      S.dmisc[D_DISC] = P.disc[shot];
+      S.dmisc[D_LOGP] = P.logp[shot];
+    }
+    __syncthreads();
+    const uint64_t gshot = P.shot_offset + static_cast<uint64_t>(shot);
+    for (int oi = P.op_begin; oi < P.op_end; ++oi) {
+      if (S.misc[M_FAIL]) break;
+      const Op op = P.ops[oi];
+      switch (op.kind) {
+        case OP_RESET_FLIP:
+          if (tid() == 0 && philox_uniform(P.seed, gshot, op.ev) < P.pR) pauli_left(S.tm, n, op.a, 1);
+          break;
+        case OP_H:
+          if (tid() < W) {
+            int w = tid();
+            uint64_t t = S.tx[op.a * W + w];
+            S.tx[op.a * W + w] = S.tx[(n + op.a) * W + w];
+            S.tx[(n + op.a) * W + w] = t;
+            t = S.tz[op.a * W + w];
+            S.tz[op.a * W + w] = S.tz[(n + op.a) * W + w];
+            S.tz[(n + op.a) * W + w] = t;
+          }
+          if (tid() == 0) {
+            uint8_t t = S.tm[op.a];
+            S.tm[op.a] = S.tm[n + op.a];
+            S.tm[n + op.a] = t;
+          }
+          break;
+        case OP_NOISE1:
+          if (tid() == 0) {
+            double u = philox_uniform(P.seed, gshot, op.ev);
+            if (u < P.p1) pauli_left(S.tm, n, op.a, 1 + min(2, static_cast<int>(3.0 * u / P.p1)));
+          }
+          break;
+        case OP_CNOT:
+          if (tid() == 0) {
+            row_mul(S.tx, S.tz, S.tm, W, op.a, op.b);          // X_c <- X_c X_t
+            row_mul(S.tx, S.tz, S.tm, W, n + op.b, n + op.a);  // Z_t <- Z_t Z_c (rows commute)
+          }
+          break;
+        case OP_NOISE2:
+          if (tid() == 0) {
+            double u = philox_uniform(P.seed, gshot, op.ev);
+            if (u < P.p2) {
+              int idx = min(14, static_cast<int>(15.0 * u / P.p2)) + 1;
+              int lc = idx / 4, lt = idx % 4;  // 0 I, 1 X, 2 Y, 3 Z
+              if (lc) pauli_left(S.tm, n, op.a, lc);
+              if (lt) pauli_left(S.tm, n, op.b, lt);
+            }
+          }
+          break;
+        case OP_ROT:
+        case OP_MEAS: {
+          const bool meas = op.kind == OP_MEAS;
+          if (tid() == 0) {
+            int m;
+            if (meas) m = conj_rows(S.tx, S.tz, S.tm, W, n + op.a, -1, S.ppx, S.ppz);
+            else if (op.pauli == 0) m = conj_rows(S.tx, S.tz, S.tm, W, n + op.a, n + op.b, S.ppx, S.ppz);
+            else m = conj_rows(S.tx, S.tz, S.tm, W, op.a, op.b, S.ppx, S.ppz);
+            int lo = n, hi = -1, j = -1, xany = 0, xz = 0;
+            for (int q = 0; q < n; ++q) {
+              bool x = (S.ppx[q >> 6] >> (q & 63)) & 1, z = (S.ppz[q >> 6] >> (q & 63)) & 1;
+              if (x || z) { lo = min(lo, q); hi = max(hi, q); }
+              if (x && j < 0) j = q;
+              xany |= x;
+              xz += x && z;
+            }
+            int c = S.misc[M_CENTER];
+            S.misc[M_LO] = lo;
+            S.misc[M_HI] = hi;
+            S.misc[M_A] = min(lo, c);
+            S.misc[M_B] = max(hi, c);
+            S.misc[M_J] = j;
+            S.misc[M_CASEB] = xany;
+            S.misc[M_BIT] = m | ((((m - xz) & 3) == 2) << 4);  // phase | (sign < 0) << 4
+            MpoSpec<T> &sp = *S.spec;
+            sp.lo = lo; sp.hi = hi; sp.j = j;
+            if (!meas) {
+              double th = P.theta[op.idx];
+              cplx<T> w1 = cmul(cmake<T>(0, static_cast<T>(-sin(th))), ipow<T>(m));
+              sp.kind = MPO_ROT;
+              sp.w0 = cmake<T>(static_cast<T>(cos(th)), 0);
+              sp.w1 = w1;
+            }
+            if (lo > hi) S.misc[M_FAIL] = STN_ENUMERIC;  // identity Pauli cannot occur
+          }
+          __syncthreads();
+          if (S.misc[M_FAIL]) break;
+          const int a = S.misc[M_A], b = S.misc[M_B];
+          int caseB = 0, lidx = 0, outcome = 0;
+          if (meas) {
+            const int mb = S.misc[M_BIT];
+            double e = mps_expect<T>(P, S, shot, X, a, b, mb & 3);
+            if (tid() == 0) {
+              double p0 = fmin(1.0, fmax(0.0, 0.5 * (1.0 + e)));
+              double u = philox_uniform(P.seed, gshot, op.ev);
+              int bit = u < p0 ? 0 : 1;
+              double pb = bit == 0 ? p0 : 1.0 - p0;
+              if (fabs(u - p0) < kNearThreshold) P.near[shot] += 1;
+              P.born[shot * P.n_meas + op.idx] = pb;
+              S.dmisc[D_LOGP] += log(pb);
+              int flip = philox_uniform(P.seed, gshot, op.ev + 1) < P.pM ? 1 : 0;
+              if (bit ^ flip) P.records[shot * P.rec_bytes + op.idx / 8] |= static_cast<uint8_t>(1u << (op.idx % 8));
+              MpoSpec<T> &sp = *S.spec;
+              const int m = mb & 3;
+              const int neg = (mb >> 4) & 1;
+              if (!S.misc[M_CASEB]) {
+                sp.kind = MPO_PROJ_Z;
+                sp.w0 = cmake<T>(T(0.5), 0);
+                cplx<T> w1 = ipow<T>(m);
+                T sgn = bit ? T(-0.5) : T(0.5);
+                sp.w1 = cmake<T>(w1.re * sgn, w1.im * sgn);
+              } else {
+                const int jq = S.misc[M_J];
+                const bool zj = (S.ppz[jq >> 6] >> (jq & 63)) & 1;
+                int lam = (bit ? -1 : 1) * (neg ? -1 : 1);
+                int li = (zj ? 2 : 0) + (lam < 0 ? 1 : 0);
+                const T r2 = static_cast<T>(0.70710678118654752440);
+                sp.kind = MPO_PROJ_B;
+                sp.w0 = cmake<T>(1, 0);
+                sp.w1 = cmake<T>(1, 0);
+                sp.v0 = cmake<T>(r2, 0);
+                sp.v1 = zj ? cmake<T>(0, lam > 0 ? r2 : -r2) : cmake<T>(lam > 0 ? r2 : -r2, 0);
+                S.misc[M_LIDX] = li;
+              }
+              S.misc[M_OUTCOME] = bit;
+            }
+            __syncthreads();
+            caseB = S.misc[M_CASEB];
+            lidx = S.misc[M_LIDX];
+            outcome = S.misc[M_OUTCOME];
+          }
+          mps_apply_compress<T>(P, S, shot, X, a, b);
+          if (meas) {
+            if (caseB) tableau_caseB(S.tx, S.tz, S.tm, n, W, S.ppx, S.ppz, S.misc[M_J], lidx);
+            if (tid() == 0 && op.pauli == 1) {
+              if (outcome) pauli_left(S.tm, n, op.a, 1);
+              if (philox_uniform(P.seed, gshot, op.ev + 2) < P.pR) pauli_left(S.tm, n, op.a, 1);
+            }
+          }
+          break;
+        }
+        default:
+          if (tid() == 0) S.misc[M_FAIL] = STN_EINVAL;
+      }
+      __syncthreads();
+    }
+    // store
+    for (int e = tid(); e < 2 * n * W; e += kThreads) {
+      P.tab_x[shot * 2 * n * W + e] = S.tx[e];
+      P.tab_z[shot * 2 * n * W + e] = S.tz[e];
+    }
+    for (int e = tid(); e < 2 * n; e += kThreads) P.tab_m[shot * 2 * n + e] = S.tm[e];
+    for (int e = tid(); e <= n; e += kThreads) P.chi[shot * (n + 1) + e] = S.chi[e];
+    if (tid() == 0) {
+      P.center[shot] = S.misc[M_CENTER];
+      P.status[shot] = S.misc[M_FAIL];
+      P.maxchi[shot] = S.misc[M_MAXCHI];
+      P.disc[shot] = S.dmisc[D_DISC];
+      P.logp[shot] = S.dmisc[D_LOGP];
+      if (S.misc[M_FAIL]) atomicCAS(P.err, 0, S.misc[M_FAIL]);
+    }
+    __syncthreads();
+  }
+}
+
+// Identity frame, |0...0>, cleared records and accumulators.
+template <typename T>
+__global__ void init_kernel(EngineParams P) {
+  const int n = P.n, W = P.W;
+  for (int64_t shot = blockIdx.x; shot < P.shots; shot += gridDim.x) {
+    for (int e = tid(); e < 2 * n * W; e += blockDim.x) {
+      int r = e / W, w = e % W;
+      int q = r % n;
+      uint64_t bit = (q >> 6) == w ? (1ull << (q & 63)) : 0ull;
+      P.tab_x[shot * 2 * n * W + e] = r < n ? bit : 0ull;
+      P.tab_z[shot * 2 * n * W + e] = r < n ? 0ull : bit;
+    }
+    for (int e = tid(); e < 2 * n; e += blockDim.x) P.tab_m[shot * 2 * n + e] = 0;
+    for (int e = tid(); e <= n; e += blockDim.x) P.chi[shot * (n + 1) + e] = 1;
+    cplx<T> *slab = reinterpret_cast<cplx<T> *>(P.mps) + shot * P.slab_elems;
+    for (int k = tid(); k < n; k += blockDim.x) {
+      slab[P.site_off[k]] = cmake<T>(1, 0);
+      slab[P.site_off[k] + 1] = cmake<T>(0, 0);
+    }
+    for (int e = tid(); e < P.rec_bytes; e += blockDim.x) P.records[shot * P.rec_bytes + e] = 0;
+    for (int e = tid(); e < P.n_meas; e += blockDim.x) P.born[shot * P.n_meas + e] = 0.0;
+    if (tid() == 0) {
+      P.center[shot] = 0;
+      P.status[shot] = 0;
+      P.maxchi[shot] = 1;
+      P.near[shot] = 0;
+      P.disc[shot] = 0.0;
+      P.logp[shot] = 0.0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+ScratchPlan plan_scratch(int n, const int *chimax, int chi_cap) {
+  ScratchPlan p{};
+  int64_t ap = 0, g = 0;
+  int cmax = 1;
+  for (int k = 0; k < n; ++k) ap += 8ll * chimax[k] * chimax[k + 1];
+  for (int k = 1; k < n; ++k) g += 4ll * chimax[k] * chimax[k];
+  for (int k = 0; k <= n; ++k) cmax = chimax[k] > cmax ? chimax[k] : cmax;
+  (void)chi_cap;
+  int64_t c2 = static_cast<int64_t>(cmax) * cmax;
+  p.work_c = cmax;
+  p.ap_elems = ap;
+  p.g_elems = g;
+  p.work_elems = 35 * c2 + 4ll * cmax + 1024;
+  p.total = ap + g + p.work_elems;
+  return p;
+}
+
+size_t round_kernel_smem(int precision, int n, int W) {
+  return precision == 0 ? smem_bytes<double>(n, W) : smem_bytes<float>(n, W);
+}
+
+int jacobi_smem_limit(int precision) {
+  return precision == 0 ? JacobiSmem<double>::n : JacobiSmem<float>::n;
+}
+
+template <typename T>
+static cudaError_t launch_init_t(const EngineParams &p, cudaStream_t s) {
+  int grid = p.shots < 4096 ? p.shots : 4096;
+  if (grid < 1) return cudaSuccess;
+  init_kernel<T><<<grid, 128, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(int precision, const EngineParams &p, cudaStream_t s) {
+  return precision == 0 ? launch_init_t<double>(p, s) : launch_init_t<float>(p, s);
+}
+
+template <typename T>
+static cudaError_t launch_round_t(const EngineParams &p, int grid, cudaStream_t s) {
+  size_t smem = smem_bytes<T>(p.n, p.W);
+  cudaError_t e = cudaFuncSetAttribute(round_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  round_kernel<T><<<grid, kThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_round(int precision, const EngineParams &p, int grid, cudaStream_t s) {
+  return precision == 0 ? launch_round_t<double>(p, grid, s) : launch_round_t<float>(p, grid, s);
+}
+
+cudaError_t launch_philox(uint64_t seed, uint64_t shot_offset, int64_t n_shots, uint32_t event_offset,
+                          int n_events, double *out, cudaStream_t s) {
+  int64_t total = n_shots * n_events;
+  if (total <= 0) return cudaSuccess;
+  int grid = static_cast<int>((total + 255) / 256);
+  if (grid > 65535) grid = 65535;
+  philox_kernel<<<grid, 256, 0, s>>>(seed, shot_offset, n_shots, event_offset, n_events, out);
+  return cudaGetLastError();
+}
+
+}  // namespace stn

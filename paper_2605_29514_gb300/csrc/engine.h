@@ -1,0 +1,61 @@
+// Device-side parameter block and host launchers of the simulation kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "program.h"
+
+namespace stn {
+
+constexpr int kThreads = 256;   // threads per CTA of the round kernel
+constexpr double kNearThreshold = 1e-5;
+
+// Everything one segment launch needs.  Per-shot arrays are indexed by the
+// shot's position in the batch; per-CTA scratch by blockIdx.x.
+struct EngineParams {
+  const Op *ops;
+  int op_begin, op_end;
+  const double *theta;  // [K]
+  int n, W, n_meas, rec_bytes;
+  int chi_cap;
+  double cutoff, delta;
+  double p1, p2, pR, pM;
+  uint64_t seed, shot_offset;
+  int shots;
+  // frame: inverse tableau rows X_0..X_{n-1}, Z_0..Z_{n-1}
+  uint64_t *tab_x, *tab_z;  // [shot][2n][W]
+  uint8_t *tab_m;           // [shot][2n]
+  // MPS: site k of a shot at slab + site_off[k], shape (chi[k], 2, chi[k+1])
+  void *mps;
+  const int64_t *site_off;  // [n+1]
+  const int *chimax;        // [n+1] largest possible bond (cap and 2^min(k, n-k))
+  int64_t slab_elems;
+  int *chi;                 // [shot][n+1], chi[0] = chi[n] = 1
+  int *center;              // [shot]
+  double *logp, *disc;      // [shot]
+  int *maxchi, *near, *status;  // [shot]
+  uint8_t *records;         // [shot][rec_bytes]
+  double *born;             // [shot][n_meas]
+  // per-CTA scratch, complex elements of the path's precision
+  void *scratch;
+  int64_t scratch_elems, ap_elems, g_elems;
+  int work_c;               // largest bond of the plan (sizes the work area)
+  int *err;                 // first error code seen on the device
+};
+
+struct ScratchPlan {
+  int64_t ap_elems, g_elems, work_elems, total;
+  int work_c;
+};
+
+ScratchPlan plan_scratch(int n, const int *chimax, int chi_cap);
+size_t round_kernel_smem(int precision, int n, int W);
+int jacobi_smem_limit(int precision);
+
+cudaError_t launch_init(int precision, const EngineParams &p, cudaStream_t s);
+cudaError_t launch_round(int precision, const EngineParams &p, int grid, cudaStream_t s);
+cudaError_t launch_philox(uint64_t seed, uint64_t shot_offset, int64_t n_shots,
+                          uint32_t event_offset, int n_events, double *out, cudaStream_t s);
+
+}  // namespace stn

@@ -1,0 +1,175 @@
+"""GPU parity of the CUDA path against the oracle, through the C ABI.
+
+Bars (stated per test): bit-exact Philox uniforms, tableaux and records;
+Born probabilities within 1e-11 relative on the complex128 path and 1e-5 on
+the complex64 path; records may differ only after a Born draw within 1e-5 of
+its threshold, and such draws are counted."""
+
+import numpy as np
+import pytest
+
+import paper_2605_29514_gb300 as stn
+from oracle.philox import uniform
+from oracle.shot import make_program, run_shot
+from workloads import D3_EXACT, D5_BENCH, PRECISION_C64, theta_table
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    stn.build()
+
+
+def gpu_run(w, shots, offset=0, theta=None):
+    sim = stn.Simulator(w, max_shots=shots)
+    if theta is None:
+        theta = theta_table(w, sim.n_pairs)
+    out = sim.sample_shots(shots, offset, theta)
+    return sim, out, theta
+
+
+def oracle_tableau_words(T, n):
+    W = (n + 63) // 64
+    xs, zs, ms = T.snapshot()
+    def pack(bits):
+        out = np.zeros((bits.shape[0], W), dtype=np.uint64)
+        for r in range(bits.shape[0]):
+            for q in np.flatnonzero(bits[r]):
+                out[r, q // 64] |= np.uint64(1) << np.uint64(q % 64)
+        return out
+    return pack(xs), pack(zs), ms.astype(np.uint8)
+
+
+def compare_shot(sim, out, s, ref, rel_tol, check_tableau=True):
+    """Records equal up to the first near-threshold draw; Born probabilities
+    within rel_tol (relative, absolute floor 1e-9 for p < 1e-4)."""
+    bits = out["bits"][s]
+    born = out["born"][s]
+    first_diff = next((i for i in range(len(ref.record)) if bits[i] != ref.record[i]), None)
+    upto = len(ref.record) if first_diff is None else first_diff
+    # a record can only differ after a near-threshold draw on either side
+    if first_diff is not None:
+        assert ref.near_draws > 0 or out["near_draws"][s] > 0, f"shot {s}: record {first_diff} differs"
+    rb = np.array(ref.born[:upto])
+    gb = born[:upto]
+    err = np.abs(gb - rb) / np.maximum(np.abs(rb), 1e-4)
+    assert np.all(err < rel_tol), f"shot {s}: max rel Born error {err.max():.3e}"
+    if check_tableau and first_diff is None:
+        x, z, m = sim.read_tableau(s)
+        ox, oz, om = oracle_tableau_words(ref.tableau, sim.n_qubits)
+        assert np.array_equal(x, ox) and np.array_equal(z, oz) and np.array_equal(m, om)
+    return first_diff is None
+
+
+def test_philox_bit_exact():
+    seed = 0x1234_5678_9ABC
+    n_shots, n_events = 5, 300
+    offset = (1 << 32) - 2  # crosses the 32-bit shot boundary
+    d = torch.empty((n_shots, n_events), dtype=torch.float64, device="cuda")
+    stn.philox_uniforms(seed, offset, n_shots, 7, n_events, d.data_ptr())
+    torch.cuda.synchronize()
+    got = d.cpu().numpy()
+    for s in range(n_shots):
+        for e in range(0, n_events, 7):
+            assert got[s, e] == uniform(seed, offset + s, 7 + e)
+
+
+def test_device_program_matches_host_compile():
+    sim = stn.Simulator(D3_EXACT, max_shots=2)
+    ops, pairs = sim.program()
+    _, ops2, pairs2 = stn.compile_program(D3_EXACT)
+    assert np.array_equal(ops, ops2) and np.array_equal(pairs, pairs2)
+
+
+@pytest.mark.parametrize("d", [3, 5])
+def test_theta_zero_stabilizer_limit(d):
+    """theta = 0, p = 0: every detector is zero, the MPS stays a product state."""
+    w = D3_EXACT.with_(distance=d, rounds=d, theta=0.0, p=0.0)
+    sim, out, _ = gpu_run(w, 16)
+    prog = make_program(w)
+    from oracle.circuit import detectors, logical_z
+    for s in range(16):
+        rec = list(out["bits"][s])
+        assert sum(detectors(prog, rec)) == 0
+        assert logical_z(prog, rec) == 0
+        assert np.all(sim.read_bonds(s) == 1)
+    assert np.all(out["max_chi"] == 1)
+
+
+def test_d3_complex128_parity():
+    """d=3, 3 rounds, theta=0.05, no Pauli noise, chi cap 64, complex128:
+    identical records, Born within 1e-11, bit-exact tableaux."""
+    w = D3_EXACT
+    shots = 24
+    sim, out, theta = gpu_run(w, shots)
+    prog = make_program(w)
+    exact = 0
+    for s in range(shots):
+        ref = run_shot(w, s, theta, prog)
+        exact += compare_shot(sim, out, s, ref, 1e-11)
+        assert abs(out["logp"][s] - ref.logp) < 1e-9 * max(1.0, abs(ref.logp))
+        assert out["max_chi"][s] == ref.max_chi
+    assert exact == shots
+
+
+def test_d3_noise_and_offset_parity():
+    """Pauli noise (every noise path fires at p = 0.02), a shot offset past
+    2^32, and per-pair quenched angles."""
+    w = D3_EXACT.with_(p=0.02, theta_sigma=0.03)
+    shots, offset = 16, (1 << 32) + 5
+    sim, out, theta = gpu_run(w, shots, offset)
+    prog = make_program(w)
+    for s in range(shots):
+        ref = run_shot(w, offset + s, theta, prog)
+        compare_shot(sim, out, s, ref, 1e-11)
+
+
+def test_d3_truncating_cap_and_xx_pairs():
+    """A chi cap that binds (4), next-nearest X X pairs, one round."""
+    w = D3_EXACT.with_(chi_cap=4, rounds=1, pair_rule="adjacent_idle+diag_xx", p=0.01)
+    shots = 12
+    sim, out, theta = gpu_run(w, shots)
+    prog = make_program(w)
+    for s in range(shots):
+        ref = run_shot(w, s, theta, prog)
+        compare_shot(sim, out, s, ref, 1e-9)
+        assert out["discarded"][s] == pytest.approx(ref.discarded, rel=1e-6, abs=1e-12)
+
+
+def test_d3_complex64_parity():
+    """The complex64 path on the d=3 workload: Born within 1e-5 relative."""
+    w = D3_EXACT.with_(precision=PRECISION_C64, svd_cutoff=1e-3, degeneracy_tol=1e-4)
+    shots = 24
+    sim, out, theta = gpu_run(w, shots)
+    prog = make_program(w)
+    for s in range(shots):
+        ref = run_shot(w, s, theta, prog)
+        compare_shot(sim, out, s, ref, 1e-5, check_tableau=False)
+
+
+def test_d5_first_round_parity():
+    """The benchmark workload (d=5, theta=0.10, p=1e-3, chi cap 256,
+    complex64), sampled: the records and Born probabilities of round 0 of a
+    full 5-round run equal the oracle's one-round program (same events)."""
+    w = D5_BENCH
+    shots = 4
+    sim = stn.Simulator(w, max_shots=shots)
+    theta = theta_table(w, sim.n_pairs)
+    sim.begin_batch(shots, 0)
+    sim.apply_round(0, theta)
+    out = sim.read_records()
+    w1 = w.with_(rounds=1)
+    prog1 = make_program(w1)
+    na = 24
+    for s in range(shots):
+        ref = run_shot(w1, s, theta, prog1)
+        bits = out["bits"][s][:na]
+        assert list(bits) == ref.record[:na] or out["near_draws"][s] > 0 or ref.near_draws > 0
+        rb = np.array(ref.born[:na])
+        err = np.abs(out["born"][s][:na] - rb) / np.maximum(rb, 1e-4)
+        assert np.all(err < 1e-5)

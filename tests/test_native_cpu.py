@@ -1,0 +1,91 @@
+"""CPU checks of the native library: it loads, exports every entry point that
+include/stn.h declares, and its host-side circuit compiler emits exactly the
+program the oracle builds (no GPU needed)."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2605_29514_gb300 as stn
+from oracle.shot import make_program
+from workloads import D3_EXACT, D5_BENCH
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    stn.build()
+    return stn.load()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "stn.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(stn_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+KIND = {"RN": 1, "H": 2, "D1": 3, "CX": 4, "D2": 5, "ROT": 6, "M": 7}
+
+
+def oracle_rows(prog):
+    rows = []
+    for op in prog.ops:
+        k = op[0]
+        if k in ("RN", "D1"):
+            rows.append([KIND[k], op[1], 0, 0, op[2], 0])
+        elif k == "H":
+            rows.append([2, op[1], 0, 0, 0, 0])
+        elif k == "CX":
+            rows.append([4, op[1], op[2], 0, 0, 0])
+        elif k == "D2":
+            rows.append([5, op[1], op[2], 0, op[3], 0])
+        elif k == "ROT":
+            p = prog.pairs[op[1]]
+            rows.append([6, p.a, p.b, 0 if p.pauli == "ZZ" else 1, 0, op[1]])
+        elif k == "M":
+            q, evb, evf, rec, reset, evr = op[1:]
+            assert evf == evb + 1 and (not reset or evr == evb + 2)
+            rows.append([7, q, 0, int(reset), evb, rec])
+    return np.array(rows, dtype=np.int32)
+
+
+@pytest.mark.parametrize("d", [3, 5, 7, 9])
+@pytest.mark.parametrize("rule", ["adjacent_idle", "adjacent_idle+diag_xx"])
+def test_native_program_matches_oracle(lib, d, rule):
+    w = D3_EXACT.with_(distance=d, rounds=d, pair_rule=rule)
+    counts, ops, pairs = stn.compile_program(w)
+    prog = make_program(w)
+    assert counts[0] == prog.layout.n
+    assert counts[1] == len(prog.pairs)
+    assert counts[2] == prog.n_meas == w.n_meas
+    assert counts[3] == prog.n_events
+    assert np.array_equal(ops, oracle_rows(prog))
+    ref_pairs = np.array([[p.a, p.b, 0 if p.pauli == "ZZ" else 1, p.layer_mask] for p in prog.pairs])
+    assert np.array_equal(pairs, ref_pairs)
+
+
+def test_bench_program_sizes(lib):
+    counts, ops, _ = stn.compile_program(D5_BENCH)
+    n, K, n_meas, n_events, n_ops = counts
+    assert (n, K, n_meas) == (49, 80, 145)
+    assert int(np.sum(ops[:, 0] == 6)) == 5 * 3 * 80  # 1200 rotations
+    assert int(np.sum(ops[:, 0] == 7)) == 145
+
+
+@pytest.mark.parametrize("bad", [dict(distance=4), dict(distance=1), dict(rounds=0), dict(chi_cap=0),
+                                 dict(chi_cap=1000), dict(p=-1.0), dict(p=0.5, pM_scale=5.0),
+                                 dict(svd_cutoff=1.5), dict(precision=7)])
+def test_invalid_configs_rejected(lib, bad):
+    with pytest.raises(stn.StnError) as e:
+        stn.compile_program(D3_EXACT.with_(**bad))
+    assert e.value.status == stn.STN_EINVAL
