@@ -85,7 +85,8 @@ def test_pauli_noise_keeps_mps_a_product_state():
 # -- dense statevector (exact, no truncation) -----------------------------------
 @pytest.mark.parametrize("rule,p", [("adjacent_idle", 0.0), ("adjacent_idle", 0.02)])
 def test_oracle_matches_dense_statevector_d3(rule, p):
-    w = D3_EXACT.with_(chi_cap=256, p=p, pair_rule=rule, theta=0.07)
+    w = D3_EXACT.with_(chi_cap=256, p=p, pair_rule=rule, theta=0.07, svd_cutoff=1e-14,
+                       degeneracy_tol=0.0)
     prog = make_program(w)
     th = theta_table(w.with_(theta_sigma=0.03), len(prog.pairs))
     for shot in range(3):
@@ -101,7 +102,7 @@ def test_oracle_matches_dense_with_xx_pairs():
     round 0, then a Z measurement of every qubit."""
     from dataclasses import replace
     w = D3_EXACT.with_(chi_cap=256, p=0.02, pair_rule="adjacent_idle+diag_xx", theta=0.08,
-                       theta_sigma=0.02)
+                       theta_sigma=0.02, svd_cutoff=1e-14, degeneracy_tol=0.0)
     prog = make_program(w)
     th = theta_table(w, len(prog.pairs))
     cut = [i for i, op in enumerate(prog.ops) if op[0] == "ROT"][40]
@@ -192,8 +193,8 @@ def test_theta_sign_invariance():
 def test_truncation_bounded_by_discarded_weight():
     """A small chi cap changes Born probabilities by an amount bounded by the
     discarded weight (Eq. 8: the dropped Schmidt terms carry that weight)."""
-    w_exact = D3_EXACT.with_(chi_cap=256)
-    w_cut = D3_EXACT.with_(chi_cap=4)
+    w_exact = D3_EXACT.with_(chi_cap=256, svd_cutoff=1e-14, degeneracy_tol=0.0)
+    w_cut = D3_EXACT.with_(chi_cap=4, svd_cutoff=1e-14, degeneracy_tol=0.0)
     prog = make_program(w_exact)
     th = theta_table(w_exact, len(prog.pairs))
     for shot in range(2):
@@ -219,7 +220,7 @@ def _dense_mismatch(w, prog, th, shots=2):
 def _some_pin_fails():
     """Run a set of pins; True when at least one of them fails."""
     import test_oracle_core as core
-    w = D3_EXACT.with_(chi_cap=256, p=0.03)
+    w = D3_EXACT.with_(chi_cap=256, p=0.03, svd_cutoff=1e-14, degeneracy_tol=0.0)
     prog = make_program(w)
     th = theta_table(w, len(prog.pairs))
     checks = [

@@ -34,8 +34,11 @@ class Workload:
     pM_scale: float = 5.0
     # Schmidt values at or below svd_cutoff * s_1 are dropped; at a chi cap,
     # kept values must exceed the first dropped one by degeneracy_tol * s_1.
-    svd_cutoff: float = 1e-6
-    degeneracy_tol: float = 1e-6
+    # A dropped value changes Born probabilities by up to its amplitude, so
+    # both sit well below the Born tolerance and well above the rounding
+    # level of the arithmetic.
+    svd_cutoff: float = 1e-12
+    degeneracy_tol: float = 1e-12
     pair_rule: str = "adjacent_idle"
     theta_sigma: float = 0.0
     theta_seed: int = 7
@@ -88,6 +91,6 @@ D5_BENCH = Workload(
     precision=PRECISION_C64,
     shots=16384,
     seed=0,
-    svd_cutoff=1e-3,
-    degeneracy_tol=1e-4,
+    svd_cutoff=5e-6,
+    degeneracy_tol=5e-6,
 )
