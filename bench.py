@@ -1,0 +1,300 @@
+"""Throughput benchmark: shots/s of d=5, 5-round crosstalk syndrome extraction
+on one GB300 (theta = 0.10 ZZ on idle adjacent pairs, depolarising p = 1e-3
+with the Table I ratios, chi cap 256, complex64 contractions).
+
+A step is one program segment (one syndrome round, or the final readout)
+applied to a batch of B shots; a batch completes after rounds + 1 = 6 steps
+and the next batch starts with new shot indices.  K is rounded up to a
+multiple of 6 so every segment is timed equally often, and
+    value = B * K / 6 / timed seconds
+is whole-shot throughput.  Inputs (angle table, program) are resident in HBM
+and records stay on the device in the timed region; `e2e` times the public
+C ABI call stn_sample_shots with host buffers (angle upload and record
+download inside the timed region).
+
+Run: python bench.py [--gpus N] [--steps K] [--warmup W] [--shots B]
+     python bench.py --impl reference    (the CPU oracle on a bounded sample)
+Under torchrun each rank simulates its own disjoint shot range (weak scaling,
+no data-path collective); the slowest rank's time is reported.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import D5_BENCH, theta_table  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--shots", type=int, default=152, help="shots per batch and rank")
+    ap.add_argument("--impl", default="stn", choices=["stn", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# -- clocks during the timed region --------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, f[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -- CPU baseline: the oracle, as it stands, on the host cores ------------------
+def _oracle_worker(args):
+    shot, budget, w_fields = args
+    from oracle.shot import ShotSim, make_program
+    from workloads import Workload
+    w = Workload(**w_fields)
+    prog = make_program(w)
+    sim = ShotSim(w, shot, theta_table(w, len(prog.pairs)), prog)
+    t0 = time.perf_counter()
+    done = 0
+    for op in prog.ops:
+        if time.perf_counter() - t0 > budget:
+            break
+        sim.step(op)
+        done += 1
+    return done, len(prog.ops), time.perf_counter() - t0
+
+
+def cpu_baseline(w, budget):
+    """Each host core runs the oracle on its own shot of the workload for
+    `budget` seconds.  Throughput counts the fraction of each shot's ops done;
+    later ops are the expensive ones (the bond dimension grows), so this is
+    an upper bound on the oracle's shots/s."""
+    import multiprocessing as mp
+    from dataclasses import asdict
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(s, budget, asdict(w)) for s in range(cores)])
+    frac = sum(d / n for d, n, _ in res)
+    secs = max(t for _, _, t in res)
+    ops_done = sum(d for d, _, _ in res)
+    return {"value": frac / secs, "unit": "shots/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} shots of {w.name}, one per core, {budget:.0f} s each: {ops_done} of "
+                      f"{cores * res[0][1]} ops done; shots/s counts completed op fractions "
+                      f"(upper bound: the remaining ops carry the large bond dimensions)"}
+
+
+def reference_arm(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    per = max(args.cpu_seconds / max(args.steps, 1), 2.0)
+    for _ in range(args.warmup):
+        pass  # the oracle has nothing to warm up; steps below are all timed
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(w, per)
+        vals.append(last["value"])
+    total = time.perf_counter() - t0
+    v = statistics.median(vals)
+    line = {"metric": "shots/s of d=5, 5-round crosstalk syndrome extraction on 1 GB300 at <=1e-5 Born error",
+            "impl": "reference", "value": v, "unit": "shots/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * total / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": w.name, "shots_per_batch": last["cores"]},
+            "cpu_baseline": {"value": v, "unit": "shots/s", "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": v, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -- GPU arm -------------------------------------------------------------------
+def main():
+    args = parse()
+    w = D5_BENCH
+    if args.impl == "reference":
+        reference_arm(args, w)
+        return
+    import torch
+    import paper_2605_29514_gb300 as stn
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    stn.build()
+    segs = w.rounds + 1
+    K = max(segs, ((args.steps + segs - 1) // segs) * segs)
+    W = max(3, args.warmup)
+    B = args.shots
+    stream = torch.cuda.current_stream()
+    sim = stn.Simulator(w, max_shots=B, stream=stream.cuda_stream)
+    theta = theta_table(w, sim.n_pairs)
+    d_theta = torch.tensor(theta, dtype=torch.float64, device="cuda")
+    base = rank * 10 ** 9  # disjoint shot ranges per rank
+
+    state = {"seg": 0, "batch": 0}
+
+    def step():
+        if state["seg"] == 0:
+            sim.begin_batch(B, base + state["batch"] * B)
+        sim.apply_round_device(state["seg"], d_theta.data_ptr())
+        state["seg"] += 1
+        if state["seg"] == segs:
+            state["seg"] = 0
+            state["batch"] += 1
+
+    # warm-up: W segments of batch 0, then a fresh batch for the timed region
+    for _ in range(W):
+        step()
+    sim.sync()
+    state["seg"], state["batch"] = 0, 1
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_host = time.perf_counter()
+    ev0.record(stream)
+    launches = 0
+    flops0 = sim.algorithmic_flops()
+    for _ in range(K):
+        if state["seg"] == 0:
+            launches += 1  # batch initialisation kernel
+        step()
+        launches += 1
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    host_s = time.perf_counter() - t_host
+    sim.sync()
+    flops = sim.algorithmic_flops() - flops0
+    clk = clocks.stop()
+    secs = ev0.elapsed_time(ev1) / 1000.0
+    if pg:
+        t = torch.tensor([secs], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        secs = float(t.item())
+    shots_done = ws * B * K // segs
+    value = shots_done / secs
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        import numpy as np
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        out = sim.sample_shots(B, base + 10 ** 8, theta, born=False, stats=True)
+        e2e_s = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": ws * B / e2e_s, "unit": "shots/s",
+               "h2d_bytes_per_step": int(theta.nbytes) // 1,
+               "d2h_bytes_per_step": int(out["records"].nbytes + B * 24) // segs,
+               "note": "stn_sample_shots: angle upload per segment, records + per-shot stats download"}
+
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    achieved = flops / secs / 1e12 / ws
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {max_mhz:.0f} MHz "
+                               "(max SM clock of MEASURED_PEAKS.json)",
+                "kernel": "stn::round_kernel<float>",
+                "work": "algorithmic FLOPs of the MPS sweeps (standard GEMM, Householder QR and SVD counts)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline(w, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": "shots/s of d=5, 5-round crosstalk syndrome extraction on 1 GB300 at <=1e-5 Born error",
+                "value": value, "unit": "shots/s", "n_gpus": ws, "steps": K, "warmup": W,
+                "ms_per_step": 1000.0 * secs / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+                "config": {"workload": w.name, "distance": w.distance, "rounds": w.rounds, "theta": w.theta,
+                           "p": w.p, "chi_cap": w.chi_cap, "shots_per_batch_per_rank": B,
+                           "step": "one program segment (syndrome round or final readout) over the batch",
+                           "l2": "per-shot MPS state (GBs) larger than L2; no flush",
+                           "parallelism": f"shots sharded over {ws} rank(s)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "host_seconds": host_s}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

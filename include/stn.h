@@ -141,6 +141,12 @@ stn_status stn_read_records(stn_ctx *ctx, uint8_t *h_records, double *h_born,
  * ([shots][ceil(n_meas/8)] bytes, owned by the context). */
 const uint8_t *stn_device_records(const stn_ctx *ctx);
 
+/* Algorithmic FLOPs of all MPS work since creation, summed over shot slots
+ * (synchronises): textbook counts of the GEMMs, Householder R factors and
+ * SVDs the sweeps perform (Sec. IV B), independent of the kernels' actual
+ * instruction mix.  Used to place measured throughput on a roofline. */
+stn_status stn_algorithmic_flops(stn_ctx *ctx, double *h_total);
+
 /* Inverse tableau of one shot of the current batch (synchronises): rows
  * X_0..X_{n-1}, Z_0..Z_{n-1}; row r is i^phase[r] X^x Z^z with x bits in
  * h_x[r*W .. r*W+W-1] (W = ceil(n/64) words, qubit q at bit q%64 of word
@@ -167,6 +173,22 @@ stn_status stn_logprob_grad(stn_ctx *ctx, const uint8_t *h_records, int64_t n_re
 stn_status stn_philox_uniforms(uint64_t seed, uint64_t shot_offset, int64_t n_shots,
                                uint32_t event_offset, int32_t n_events, double *d_out,
                                void *cuda_stream);
+
+/* Dense building blocks of the truncation sweep (Sec. IV B, Eq. 8), run alone
+ * on one CTA for checking.  precision: STN_PRECISION_*; complex elements are
+ * interleaved (re, im) of that precision, all device memory.
+ * stn_dense_qr: Householder QR of d_b (m x n, row-major, m <= 1024), in
+ *   place; rows 0..min(m,n)-1 then hold R, the rest is zero.
+ * stn_dense_svd: one-sided Jacobi SVD of d_c (m x n, column-major, n <= 512):
+ *   d_c becomes U diag(sigma), d_v (n x n, column-major) the right singular
+ *   vectors, d_sig2[n] (real, of the precision) sigma^2, unsorted.
+ *   in_shared = 1 runs it in shared memory (requires m n + n^2 to fit);
+ *   in_shared = 2 runs the blocked variant (column-block pairs in shared
+ *   memory, C and V in global memory), the one used for large bonds.
+ * Errors: STN_EINVAL on bad sizes, STN_ECUDA on launch failure. */
+stn_status stn_dense_qr(int32_t precision, int32_t m, int32_t n, void *d_b, void *cuda_stream);
+stn_status stn_dense_svd(int32_t precision, int32_t m, int32_t n, void *d_c, void *d_v, void *d_sig2,
+                         int32_t in_shared, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -112,6 +112,11 @@ class Simulator:
             out["logp"] = np.array([x.logp for x in s])
         return out
 
+    def algorithmic_flops(self):
+        v = ctypes.c_double()
+        self._check(self.lib.stn_algorithmic_flops(self.ctx, ctypes.byref(v)))
+        return v.value
+
     def device_records_ptr(self):
         return self.lib.stn_device_records(self.ctx)
 
@@ -173,5 +178,18 @@ def philox_uniforms(seed, shot_offset, n_shots, event_offset, n_events, d_out_pt
         raise StnError(st, "stn_philox_uniforms failed")
 
 
+def dense_qr(precision, m, n, d_b, stream=0):
+    st = load().stn_dense_qr(int(precision), int(m), int(n), ctypes.c_void_p(d_b), ctypes.c_void_p(stream))
+    if st != STN_OK:
+        raise StnError(st, "stn_dense_qr failed")
+
+
+def dense_svd(precision, m, n, d_c, d_v, d_sig2, in_shared, stream=0):
+    st = load().stn_dense_svd(int(precision), int(m), int(n), ctypes.c_void_p(d_c), ctypes.c_void_p(d_v),
+                              ctypes.c_void_p(d_sig2), int(in_shared), ctypes.c_void_p(stream))
+    if st != STN_OK:
+        raise StnError(st, "stn_dense_svd failed")
+
+
 __all__ = ["Simulator", "StnError", "build", "load", "philox_uniforms", "unpack_records",
-           "config_from_workload", "compile_program"]
+           "config_from_workload", "compile_program", "dense_qr", "dense_svd"]

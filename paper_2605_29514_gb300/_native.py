@@ -97,6 +97,7 @@ EXPORTS = [
     ("stn_read_records", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p]),
     ("stn_device_records", ctypes.c_void_p, [ctypes.c_void_p]),
+    ("stn_algorithmic_flops", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("stn_read_tableau", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p]),
     ("stn_read_bonds", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
@@ -105,6 +106,10 @@ EXPORTS = [
                                         ctypes.c_void_p]),
     ("stn_logprob_grad", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("stn_dense_qr", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
+    ("stn_dense_svd", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     ("stn_philox_uniforms", ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                            ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p,
                                            ctypes.c_void_p]),

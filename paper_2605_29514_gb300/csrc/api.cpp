@@ -20,7 +20,7 @@ struct stn_ctx {
   cudaStream_t stream = nullptr;
   int64_t max_shots = 0, shots = 0;
   uint64_t shot_offset = 0;
-  int n = 0, W = 0, rec_bytes = 0, K = 0, grid = 1;
+  int n = 0, W = 0, rec_bytes = 0, K = 0, grid = 1, svd_elems = 0;
   std::vector<int> chimax;
   std::vector<int64_t> site_off;
   int64_t slab_elems = 0;
@@ -36,7 +36,7 @@ struct stn_ctx {
   int *d_chimax = nullptr;
   int *d_chi = nullptr, *d_center = nullptr, *d_maxchi = nullptr, *d_near = nullptr,
       *d_status = nullptr;
-  double *d_logp = nullptr, *d_disc = nullptr, *d_born = nullptr;
+  double *d_logp = nullptr, *d_disc = nullptr, *d_born = nullptr, *d_flops = nullptr;
   uint8_t *d_rec = nullptr;
   void *d_scratch = nullptr;
   int *d_err = nullptr;
@@ -102,11 +102,13 @@ stn::EngineParams params(const stn_ctx *c, int seg, const double *d_theta) {
   p.status = c->d_status;
   p.records = c->d_rec;
   p.born = c->d_born;
+  p.flops = c->d_flops;
   p.scratch = c->d_scratch;
   p.scratch_elems = c->plan.total;
   p.ap_elems = c->plan.ap_elems;
   p.g_elems = c->plan.g_elems;
   p.work_c = c->plan.work_c;
+  p.svd_elems = c->svd_elems;
   p.err = c->d_err;
   return p;
 }
@@ -167,6 +169,11 @@ stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_strea
     c->site_off[k + 1] = c->site_off[k] + 2ll * c->chimax[k] * c->chimax[k + 1];
   c->slab_elems = c->site_off[n];
   c->plan = stn::plan_scratch(n, c->chimax.data(), cfg->chi_cap);
+  c->svd_elems = stn::round_kernel_svd_elems(cfg->precision, n, c->W);
+  if (c->svd_elems < 2 * 4 * c->plan.work_c + 16) {  // the blocked SVD needs two columns
+    delete c;
+    return STN_EINVAL;
+  }
 
   int dev = 0, sms = 1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -197,6 +204,7 @@ stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_strea
   A(dalloc(c, &c->d_logp, sizeof(double) * S));
   A(dalloc(c, &c->d_disc, sizeof(double) * S));
   A(dalloc(c, &c->d_born, sizeof(double) * S * c->prog.n_meas));
+  A(dalloc(c, &c->d_flops, sizeof(double) * S));
   A(dalloc(c, &c->d_rec, static_cast<size_t>(S) * c->rec_bytes));
   A(dalloc(c, &c->d_scratch, c->elem * static_cast<size_t>(c->grid) * c->plan.total));
   A(dalloc(c, &c->d_err, sizeof(int)));
@@ -214,6 +222,7 @@ stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_strea
     e = cudaMemcpyAsync(c->d_chimax, c->chimax.data(), sizeof(int) * (n + 1),
                         cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_flops, 0, sizeof(double) * S, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     stn_destroy(c);
@@ -355,6 +364,19 @@ stn_status stn_read_records(stn_ctx *c, uint8_t *h_records, double *h_born,
 
 const uint8_t *stn_device_records(const stn_ctx *c) { return c ? c->d_rec : nullptr; }
 
+stn_status stn_algorithmic_flops(stn_ctx *c, double *h_total) {
+  if (!c || !h_total) return STN_EINVAL;
+  stn_status st = stn_sync(c);
+  if (st != STN_OK) return st;
+  std::vector<double> f(c->max_shots);
+  cudaError_t e = cudaMemcpy(f.data(), c->d_flops, sizeof(double) * c->max_shots, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stn_algorithmic_flops");
+  double t = 0;
+  for (double v : f) t += v;
+  *h_total = t;
+  return STN_OK;
+}
+
 stn_status stn_read_tableau(stn_ctx *c, int64_t shot, uint64_t *h_x, uint64_t *h_z,
                             uint8_t *h_phase) {
   if (!c || shot < 0 || shot >= c->shots) return fail(c, STN_EINVAL, "shot out of range");
@@ -394,6 +416,25 @@ stn_status stn_sample_shots(stn_ctx *c, int64_t shots, uint64_t shot_offset, con
 stn_status stn_logprob_grad(stn_ctx *c, const uint8_t *, int64_t, const double *, double *,
                             double *) {
   return fail(c, STN_ENOTIMPL, "stn_logprob_grad is not implemented");
+}
+
+stn_status stn_dense_qr(int32_t precision, int32_t m, int32_t n, void *d_b, void *cuda_stream) {
+  if ((precision != 0 && precision != 1) || m < 1 || n < 1 || m > 1024 || !d_b) return STN_EINVAL;
+  cudaError_t e = stn::launch_dense_check(precision, 0, m, n, d_b, nullptr, nullptr, 0,
+                                          static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? STN_OK : STN_ECUDA;
+}
+
+stn_status stn_dense_svd(int32_t precision, int32_t m, int32_t n, void *d_c, void *d_v, void *d_sig2,
+                         int32_t in_shared, void *cuda_stream) {
+  if ((precision != 0 && precision != 1) || m < 1 || n < 1 || n > 512 || !d_c || !d_v || !d_sig2)
+    return STN_EINVAL;
+  if (in_shared == 1 && m * n + n * n > stn::svd_smem_elems(precision)) return STN_EINVAL;
+  if (in_shared < 0 || in_shared > 2 || (in_shared == 2 && 2 * m + 4 > stn::svd_smem_elems(precision)))
+    return STN_EINVAL;
+  cudaError_t e = stn::launch_dense_check(precision, 1, m, n, d_c, d_v, d_sig2, in_shared,
+                                          static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? STN_OK : STN_ECUDA;
 }
 
 stn_status stn_philox_uniforms(uint64_t seed, uint64_t shot_offset, int64_t n_shots,

@@ -83,20 +83,21 @@ struct Eps<double> {
   static constexpr double v = 1.11e-16;
 };
 
-// Matrices that fit this size are diagonalised in shared memory.
+// Complex elements of shared memory for the one-sided Jacobi SVD (the matrix
+// and its right singular vectors); larger problems run on global scratch.
 template <typename T>
-struct JacobiSmem;
+struct SvdSmem;
 template <>
-struct JacobiSmem<float> {
-  static constexpr int n = 80;
+struct SvdSmem<float> {
+  static constexpr int elems = 22528;
 };
 template <>
-struct JacobiSmem<double> {
-  static constexpr int n = 48;
+struct SvdSmem<double> {
+  static constexpr int elems = 8192;
 };
+constexpr int kMaxVec = 1024;  // longest Householder vector (4 * largest bond)
 
 constexpr int kBM = 64, kBN = 64, kBK = 16, kPad = 4;
-constexpr int kMaxPairs = 256;  // Jacobi pairs per round: n <= 512
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): two 32x32->64-bit
@@ -223,103 +224,270 @@ __device__ void cgemm(int M, int N, int K, cplx<T> alpha, const cplx<T> *A, int 
   __syncthreads();
 }
 
-template <typename T>
-struct RotParam {
-  int p, q, skip;
-  T cs, sn, shift;  // shift = t |c|
-  cplx<T> u;        // phase of A[p][q]
-};
+__device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+constexpr int kWarps = kThreads / 32;
 
-// Hermitian eigendecomposition A = V diag(lambda) V^dag by cyclic Jacobi with
-// the round-robin parallel ordering (n/2 disjoint rotations per step).  A is
-// overwritten (it becomes diagonal).  A and V may live in shared or global
-// memory.
 template <typename T>
-__device__ void jacobi_heev(int n, cplx<T> *A, int lda, cplx<T> *V, int ldv, RotParam<T> *rp,
-                            int *flag, double *red) {
-  double tr = 0;
-  for (int e = tid(); e < n * n; e += kThreads) {
-    int i = e / n, j = e % n;
-    V[i * ldv + j] = cmake<T>(i == j ? T(1) : T(0), 0);
-    if (i == j) tr += fabs(static_cast<double>(A[i * lda + i].re));
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Householder QR of B (m x n, row-major, leading dimension ld), in place: on
+// return rows 0..min(m,n)-1 hold R (upper trapezoidal) and the rest is zero.
+// Each step uses the Hermitian reflector P = I - 2 u u^dag with
+// P x = gamma e_1, gamma = -(x_0/|x_0|) ||x||.  CTA-wide; u lives in `uv`.
+template <typename T>
+__device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *uv, double *red,
+                             double *dm) {
+  const int steps = min(m, n);
+  for (int j = 0; j < steps; ++j) {
+    double nx2 = 0;
+    for (int i = j + tid(); i < m; i += kThreads) nx2 += static_cast<double>(cabs2(B[static_cast<int64_t>(i) * ld + j]));
+    nx2 = block_sum(nx2, red);
+    if (!(nx2 > 0.0)) continue;  // zero column: R row j is already final
+    if (tid() == 0) {
+      cplx<T> al = B[static_cast<int64_t>(j) * ld + j];
+      double aa = sqrt(static_cast<double>(cabs2(al)));
+      double nx = sqrt(nx2);
+      double pr = aa > 0 ? al.re / aa : 1.0, pi = aa > 0 ? al.im / aa : 0.0;
+      dm[0] = -pr * nx;  // gamma
+      dm[1] = -pi * nx;
+      dm[2] = 1.0 / sqrt(2.0 * nx * (nx + aa));  // 1 / ||x - gamma e_1||
+    }
+    __syncthreads();
+    const cplx<T> gam = cmake<T>(static_cast<T>(dm[0]), static_cast<T>(dm[1]));
+    const T sc = static_cast<T>(dm[2]);
+    for (int i = j + tid(); i < m; i += kThreads) {
+      cplx<T> x = B[static_cast<int64_t>(i) * ld + j];
+      if (i == j) x = cmake<T>(x.re - gam.re, x.im - gam.im);
+      uv[i - j] = cscale(x, sc);
+    }
+    __syncthreads();
+    // trailing columns: B[:, c] -= 2 u (u^dag B[:, c]), one thread per column
+    for (int c = j + 1 + tid(); c < n; c += kThreads) {
+      cplx<T> sdot = cmake<T>(0, 0);
+      for (int i = j; i < m; ++i) cfma(sdot, cconj(uv[i - j]), B[static_cast<int64_t>(i) * ld + c]);
+      sdot = cscale(sdot, T(2));
+      for (int i = j; i < m; ++i) {
+        cplx<T> &b = B[static_cast<int64_t>(i) * ld + c];
+        cplx<T> t = cmul(uv[i - j], sdot);
+        b = cmake<T>(b.re - t.re, b.im - t.im);
+      }
+    }
+    for (int i = j + tid(); i < m; i += kThreads)
+      B[static_cast<int64_t>(i) * ld + j] = i == j ? gam : cmake<T>(0, 0);
+    __syncthreads();
   }
-  tr = block_sum(tr, red);
-  if (n == 1) return;
-  const int m = n + (n & 1);
-  const int half = m / 2;
-  const T eps = Eps<T>::v;
-  // rotations below this size are skipped: they move eigenvalues by less
-  // than eps * trace
-  const T floor_abs = static_cast<T>(1e-3 * static_cast<double>(eps) * tr);
-  const int max_sweeps = sizeof(T) == 4 ? 15 : 20;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+}
+
+// One-sided (Hestenes) Jacobi SVD.  Columns of C (m x n, column-major,
+// leading dimension m) are rotated pairwise until mutually orthogonal, so
+// that C V = U diag(sigma); V (column-major) accumulates the rotations.
+// Round-robin ordering, one warp per column pair, the pairs of a round are
+// disjoint.  A pair is left alone when its columns are orthogonal to the
+// rounding level of their dot products, or when one column is negligible
+// (norm at the rounding level of ||C||: no information, and its dot products
+// would underflow).
+
+// One sweep over all column pairs of C (ldc = m) with V (n x n, ld = ldv).
+// Sets *flag when a rotation happened.  CTA-wide.
+template <typename T>
+__device__ void onesided_sweep(int m, int n, cplx<T> *C, cplx<T> *V, int ldv, T tol, T negligible,
+                               int *flag) {
+  const int mm = n + (n & 1);
+  const int half = mm / 2;
+  for (int round = 0; round < mm - 1; ++round) {
+    for (int pi = warp_id(); pi < half; pi += kWarps) {
+      int p, q;
+      if (pi == 0) { p = mm - 1; q = round; }
+      else { p = (round + pi) % (mm - 1); q = (round - pi + (mm - 1)) % (mm - 1); }
+      if (p > q) { int t = p; p = q; q = t; }
+      if (q >= n) continue;
+      cplx<T> *cp = C + static_cast<int64_t>(p) * m, *cq = C + static_cast<int64_t>(q) * m;
+      T al = 0, be = 0, gr = 0, gi = 0;
+      for (int i = lane_id(); i < m; i += 32) {
+        cplx<T> x = cp[i], y = cq[i];
+        al += cabs2(x);
+        be += cabs2(y);
+        gr += x.re * y.re + x.im * y.im;  // conj(x) y
+        gi += x.re * y.im - x.im * y.re;
+      }
+      al = __shfl_sync(0xffffffffu, warp_sum(al), 0);
+      be = __shfl_sync(0xffffffffu, warp_sum(be), 0);
+      gr = __shfl_sync(0xffffffffu, warp_sum(gr), 0);
+      gi = __shfl_sync(0xffffffffu, warp_sum(gi), 0);
+      if (!(al > negligible) || !(be > negligible)) continue;
+      T absg = sqrt(gr * gr + gi * gi);
+      if (!(absg > tol * sqrt(al) * sqrt(be))) continue;
+      T zeta = (be - al) / (T(2) * absg);
+      T az = fabs(zeta);
+      T t = az > T(1e10) ? T(0.5) / az : T(1) / (az + sqrt(T(1) + zeta * zeta));
+      if (zeta < 0) t = -t;
+      T cs = T(1) / sqrt(T(1) + t * t), sn = t * cs;
+      cplx<T> uc = cmake<T>(gr / absg, -gi / absg);  // conj(gamma / |gamma|)
+      for (int i = lane_id(); i < m; i += 32) {
+        cplx<T> x = cp[i], y = cmul(uc, cq[i]);
+        cp[i] = cmake<T>(cs * x.re - sn * y.re, cs * x.im - sn * y.im);
+        cq[i] = cmake<T>(sn * x.re + cs * y.re, sn * x.im + cs * y.im);
+      }
+      cplx<T> *vp = V + static_cast<int64_t>(p) * ldv, *vq = V + static_cast<int64_t>(q) * ldv;
+      for (int i = lane_id(); i < n; i += 32) {
+        cplx<T> x = vp[i], y = cmul(uc, vq[i]);
+        vp[i] = cmake<T>(cs * x.re - sn * y.re, cs * x.im - sn * y.im);
+        vq[i] = cmake<T>(sn * x.re + cs * y.re, sn * x.im + cs * y.im);
+      }
+      if (lane_id() == 0) *flag = 1;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T onesided_tol(int m) {
+  return Eps<T>::v * T(4) * sqrt(static_cast<T>(m > 1 ? m : 1));
+}
+
+template <typename T>
+__device__ T onesided_prologue(int m, int n, const cplx<T> *C, cplx<T> *V, double *red) {
+  for (int e = tid(); e < n * n; e += kThreads) {
+    int j = e / n, i = e % n;
+    V[e] = cmake<T>(i == j ? T(1) : T(0), 0);
+  }
+  double fro2 = 0;
+  for (int64_t e = tid(); e < static_cast<int64_t>(m) * n; e += kThreads) fro2 += static_cast<double>(cabs2(C[e]));
+  fro2 = block_sum(fro2, red);
+  return static_cast<T>(static_cast<double>(Eps<T>::v) * static_cast<double>(Eps<T>::v) * fro2);
+}
+
+template <typename T>
+__device__ void onesided_epilogue(int m, int n, const cplx<T> *C, T *sig2) {
+  for (int j = warp_id(); j < n; j += kWarps) {
+    double a = 0;
+    for (int i = lane_id(); i < m; i += 32) a += static_cast<double>(cabs2(C[static_cast<int64_t>(j) * m + i]));
+    a = warp_sum(a);
+    if (lane_id() == 0) sig2[j] = static_cast<T>(a);
+  }
+  __syncthreads();
+}
+
+constexpr int kMaxSweepsF = 15, kMaxSweepsD = 20;
+
+// Unblocked: C and V wherever they are (shared memory for small problems).
+template <typename T>
+__device__ void svd_onesided(int m, int n, cplx<T> *C, cplx<T> *V, T *sig2, int *flag, double *red) {
+  const T negligible = onesided_prologue<T>(m, n, C, V, red);
+  const T tol = onesided_tol<T>(m);
+  const int max_sweeps = sizeof(T) == 4 ? kMaxSweepsF : kMaxSweepsD;
+  for (int sweep = 0; sweep < max_sweeps && n > 1; ++sweep) {
     if (tid() == 0) *flag = 0;
     __syncthreads();
-    for (int round = 0; round < m - 1; ++round) {
-      for (int pi = tid(); pi < half; pi += kThreads) {
-        int p, q;
-        if (pi == 0) { p = m - 1; q = round; }
-        else { p = (round + pi) % (m - 1); q = (round - pi + (m - 1)) % (m - 1); }
-        if (p > q) { int t = p; p = q; q = t; }
-        RotParam<T> r;
-        r.p = p; r.q = q; r.skip = 1; r.cs = 1; r.sn = 0; r.shift = 0; r.u = cmake<T>(1, 0);
-        if (q < n) {
-          T a = A[p * lda + p].re, b = A[q * lda + q].re;
-          cplx<T> c = A[p * lda + q];
-          T absc = sqrt(cabs2(c));
-          T scale = fabs(a) + fabs(b);
-          if (absc > eps * scale * T(0.5) && absc > floor_abs) {
-            T zeta = (b - a) / (T(2) * absc);
-            T t = (zeta >= 0 ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-            r.cs = T(1) / sqrt(T(1) + t * t);
-            r.sn = t * r.cs;
-            r.shift = t * absc;
-            r.u = cmake<T>(c.re / absc, c.im / absc);
-            r.skip = 0;
-            *flag = 1;
-          }
-        }
-        rp[pi] = r;
-      }
-      __syncthreads();
-      // rows: A <- J^dag A; row p' = cs row_p - sn u row_q, row q' = sn row_p + cs u row_q
-      for (int e = tid(); e < half * n; e += kThreads) {
-        const RotParam<T> &r = rp[e / n];
-        if (r.skip) continue;
-        int j = e % n;
-        cplx<T> ap = A[r.p * lda + j], aq = A[r.q * lda + j];
-        cplx<T> uaq = cmul(r.u, aq);
-        A[r.p * lda + j] = cmake<T>(r.cs * ap.re - r.sn * uaq.re, r.cs * ap.im - r.sn * uaq.im);
-        A[r.q * lda + j] = cmake<T>(r.sn * ap.re + r.cs * uaq.re, r.sn * ap.im + r.cs * uaq.im);
-      }
-      __syncthreads();
-      // columns of A and V: col p' = cs col_p - sn conj(u) col_q, col q' = sn col_p + cs conj(u) col_q
-      for (int e = tid(); e < half * n; e += kThreads) {
-        const RotParam<T> &r = rp[e / n];
-        if (r.skip) continue;
-        int i = e % n;
-        cplx<T> uc = cconj(r.u);
-        cplx<T> ap = A[i * lda + r.p], aq = cmul(uc, A[i * lda + r.q]);
-        A[i * lda + r.p] = cmake<T>(r.cs * ap.re - r.sn * aq.re, r.cs * ap.im - r.sn * aq.im);
-        A[i * lda + r.q] = cmake<T>(r.sn * ap.re + r.cs * aq.re, r.sn * ap.im + r.cs * aq.im);
-        cplx<T> vp = V[i * ldv + r.p], vq = cmul(uc, V[i * ldv + r.q]);
-        V[i * ldv + r.p] = cmake<T>(r.cs * vp.re - r.sn * vq.re, r.cs * vp.im - r.sn * vq.im);
-        V[i * ldv + r.q] = cmake<T>(r.sn * vp.re + r.cs * vq.re, r.sn * vp.im + r.cs * vq.im);
-      }
-      __syncthreads();
-      for (int pi = tid(); pi < half; pi += kThreads) {
-        const RotParam<T> &r = rp[pi];
-        if (r.skip) continue;
-        // the 2x2 pivot block is diagonal in exact arithmetic
-        A[r.p * lda + r.q] = cmake<T>(0, 0);
-        A[r.q * lda + r.p] = cmake<T>(0, 0);
-      }
-      __syncthreads();
-    }
+    onesided_sweep<T>(m, n, C, V, n, tol, negligible, flag);
     int f = *flag;
     __syncthreads();
     if (!f) break;
   }
+  onesided_epilogue<T>(m, n, C, sig2);
+}
+
+// Blocked, for problems larger than shared memory: C and V in global memory;
+// the columns are split into blocks of bw, and every pair of blocks is
+// loaded into shared memory (sbuf), swept once there while a small unitary Q
+// (w x w) accumulates its rotations, written back, and applied to the
+// matching columns of V (V <- V Q, one thread per row).  Outer sweeps over
+// all block pairs repeat until no block pair rotates.
+template <typename T>
+__device__ void svd_onesided_blocked(int m, int n, cplx<T> *C, cplx<T> *V, T *sig2, int *flag,
+                                     double *red, cplx<T> *sbuf, int sbuf_elems) {
+  const T negligible = onesided_prologue<T>(m, n, C, V, red);
+  const T tol = onesided_tol<T>(m);
+  int bw = 32;
+  while (bw > 1 && static_cast<int64_t>(m) * 2 * bw + 4 * bw * bw > sbuf_elems) --bw;
+  const int nb = (n + bw - 1) / bw, nbe = nb + (nb & 1);
+  const int max_sweeps = sizeof(T) == 4 ? kMaxSweepsF : kMaxSweepsD;
+  cplx<T> *Cb = sbuf;
+  int *any = flag + 1;
+  for (int sweep = 0; sweep < max_sweeps && n > 1; ++sweep) {
+    if (tid() == 0) *any = 0;
+    __syncthreads();
+    for (int round = 0; round < nbe - 1; ++round) {
+      for (int bp = 0; bp < nbe / 2; ++bp) {
+        int I, J;
+        if (bp == 0) { I = nbe - 1; J = round; }
+        else { I = (round + bp) % (nbe - 1); J = (round - bp + (nbe - 1)) % (nbe - 1); }
+        if (I > J) { int t = I; I = J; J = t; }
+        if (J >= nb) continue;
+        const int c0 = I * bw, wI = min(bw, n - c0), c1 = J * bw, wJ = min(bw, n - c1);
+        const int w = wI + wJ;
+        cplx<T> *Q = Cb + static_cast<int64_t>(m) * w;
+        for (int e = tid(); e < m * w; e += kThreads) {
+          int c = e / m, i = e % m;
+          int gc = c < wI ? c0 + c : c1 + (c - wI);
+          Cb[e] = C[static_cast<int64_t>(gc) * m + i];
+        }
+        for (int e = tid(); e < w * w; e += kThreads) Q[e] = cmake<T>((e / w) == (e % w) ? T(1) : T(0), 0);
+        // up to three sweeps inside the block pair: one alone converges too
+        // slowly over the outer sweeps
+        int rotated = 0;
+        for (int inner = 0; inner < 3; ++inner) {
+          if (tid() == 0) *flag = 0;
+          __syncthreads();
+          onesided_sweep<T>(m, w, Cb, Q, w, tol, negligible, flag);
+          const int f = *flag;
+          __syncthreads();
+          if (!f) break;
+          rotated = 1;
+        }
+        if (!rotated) continue;
+        for (int e = tid(); e < m * w; e += kThreads) {
+          int c = e / m, i = e % m;
+          int gc = c < wI ? c0 + c : c1 + (c - wI);
+          C[static_cast<int64_t>(gc) * m + i] = Cb[e];
+        }
+        for (int i = tid(); i < n; i += kThreads) {
+          cplx<T> row[64];
+#pragma unroll 4
+          for (int c = 0; c < w; ++c) {
+            int gc = c < wI ? c0 + c : c1 + (c - wI);
+            row[c] = V[static_cast<int64_t>(gc) * n + i];
+          }
+          for (int c = 0; c < w; ++c) {
+            cplx<T> acc = cmake<T>(0, 0);
+            for (int j = 0; j < w; ++j) cfma(acc, row[j], Q[static_cast<int64_t>(c) * w + j]);
+            int gc = c < wI ? c0 + c : c1 + (c - wI);
+            V[static_cast<int64_t>(gc) * n + i] = acc;
+          }
+        }
+        if (tid() == 0) *any = 1;
+        __syncthreads();
+      }
+    }
+    int f = *any;
+    __syncthreads();
+    if (!f) break;
+  }
+  onesided_epilogue<T>(m, n, C, sig2);
+}
+
+// One Newton-Schulz step X <- X (3 I - X^dag X) / 2 on the k orthonormal-to-
+// rounding columns of X (n x k, row-major, ld k): the accumulated rotations
+// leave X orthonormal only to about sqrt(#rotations) eps; this brings it back
+// to the rounding level of one product.  G and Y are k x k and n x k scratch.
+template <typename T>
+__device__ void reorthonormalize(int n, int k, cplx<T> *X, cplx<T> *G, cplx<T> *Y, cplx<T> *tile) {
+  const cplx<T> one = cmake<T>(1, 0), zero = cmake<T>(0, 0);
+  cgemm<T, 1, 0>(k, k, n, one, X, k, X, k, zero, G, k, tile);
+  for (int e = tid(); e < k * k; e += kThreads) {
+    int i = e / k, j = e % k;
+    cplx<T> g = G[e];
+    G[e] = cmake<T>((i == j ? T(1.5) : T(0)) - T(0.5) * g.re, -T(0.5) * g.im);
+  }
+  __syncthreads();
+  cgemm<T, 0, 0>(n, k, k, one, X, k, G, k, zero, Y, k, tile);
+  for (int e = tid(); e < n * k; e += kThreads) X[e] = Y[e];
+  __syncthreads();
 }
 
 // Descending order of lambda (ties by index): perm[rank] = index.
@@ -392,15 +560,14 @@ struct Smem {
   double *red;
   double *dmisc;
   cplx<T> *tile;
-  RotParam<T> *rp;
-  cplx<T> *jA, *jV;
+  cplx<T> *jbuf, *uvec;
+  int *rdim;
   T *lam;
   MpoSpec<T> *spec;
 };
 
 template <typename T>
-__host__ __device__ size_t smem_bytes(int n, int W) {
-  const int NS = JacobiSmem<T>::n;
+__host__ __device__ size_t smem_bytes(int n, int W, int svd_elems) {
   size_t b = 0;
   auto add = [&](size_t bytes) { b += (bytes + 15) & ~size_t(15); };
   add(sizeof(uint64_t) * 2 * n * W);  // tx
@@ -414,19 +581,18 @@ __host__ __device__ size_t smem_bytes(int n, int W) {
   add(sizeof(int64_t) * (n + 2));     // off
   add(sizeof(int64_t) * (n + 2));     // goff
   add(sizeof(double) * kThreads);     // red
-  add(sizeof(double) * 8);            // dmisc
+  add(sizeof(double) * 16);           // dmisc
   add(sizeof(cplx<T>) * kBK * (kBM + kPad + kBN + kPad));  // tile
-  add(sizeof(RotParam<T>) * kMaxPairs);
-  add(sizeof(cplx<T>) * NS * NS);     // jA
-  add(sizeof(cplx<T>) * NS * NS);     // jV
+  add(sizeof(cplx<T>) * svd_elems);  // jbuf
+  add(sizeof(cplx<T>) * kMaxVec);     // uvec
+  add(sizeof(int) * (n + 2));         // rdim
   add(sizeof(T) * 512);               // lam
   add(sizeof(MpoSpec<T>));
   return b;
 }
 
 template <typename T>
-__device__ Smem<T> carve(char *base, int n, int W) {
-  const int NS = JacobiSmem<T>::n;
+__device__ Smem<T> carve(char *base, int n, int W, int svd_elems) {
   Smem<T> s;
   size_t b = 0;
   auto take = [&](size_t bytes) {
@@ -445,20 +611,20 @@ __device__ Smem<T> carve(char *base, int n, int W) {
   s.off = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (n + 2)));
   s.goff = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (n + 2)));
   s.red = reinterpret_cast<double *>(take(sizeof(double) * kThreads));
-  s.dmisc = reinterpret_cast<double *>(take(sizeof(double) * 8));
+  s.dmisc = reinterpret_cast<double *>(take(sizeof(double) * 16));
   s.tile = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * kBK * (kBM + kPad + kBN + kPad)));
-  s.rp = reinterpret_cast<RotParam<T> *>(take(sizeof(RotParam<T>) * kMaxPairs));
-  s.jA = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * NS * NS));
-  s.jV = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * NS * NS));
+  s.jbuf = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * svd_elems));
+  s.uvec = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * kMaxVec));
+  s.rdim = reinterpret_cast<int *>(take(sizeof(int) * (n + 2)));
   s.lam = reinterpret_cast<T *>(take(sizeof(T) * 512));
   s.spec = reinterpret_cast<MpoSpec<T> *>(take(sizeof(MpoSpec<T>)));
   return s;
 }
 
 // misc slots
-enum { M_LO = 0, M_HI, M_A, M_B, M_CENTER, M_FAIL, M_JFLAG, M_KEEP, M_MAXCHI, M_CASEB, M_J, M_BIT, M_LIDX, M_OUTCOME };
+enum { M_LO = 0, M_HI, M_A, M_B, M_CENTER, M_FAIL, M_KEEP, M_MAXCHI, M_CASEB, M_J, M_BIT, M_LIDX, M_OUTCOME, M_JFLAG };
 // dmisc slots
-enum { D_DISC = 0, D_LOGP, D_E, D_NORM };
+enum { D_DISC = 0, D_LOGP, D_E, D_NORM, D_FLOPS = 8 };
 
 // Per-CTA scratch partition (complex elements).
 template <typename T>
@@ -486,6 +652,20 @@ __device__ Scratch<T> scratch_for(const EngineParams &P, int cap) {
   s.te = s.sa + 2 * c2;
   s.lam = reinterpret_cast<T *>(s.te + 2 * c2);
   return s;
+}
+
+// Algorithmic FLOP counts (real flops of the textbook algorithm, complex = 4
+// real multiply-adds per multiply-add): a GEMM is 8 M N K, a Householder R
+// factor of an m x n matrix 4 (2 m n^2 - 2 n^3 / 3) with m >= n (roles
+// swapped otherwise), the singular values and right vectors of an m x n
+// matrix 4 (4 m n^2 + 8 n^3).
+__device__ __forceinline__ double gemm_flops(int M, int N, int K) { return 8.0 * M * N * K; }
+__device__ __forceinline__ double qr_flops(int m, int n) {
+  double a = m >= n ? m : n, b = m >= n ? n : m;
+  return 4.0 * (2.0 * a * b * b - 2.0 * b * b * b / 3.0);
+}
+__device__ __forceinline__ double svd_flops(int m, int n) {
+  return 4.0 * (4.0 * m * static_cast<double>(n) * n + 8.0 * static_cast<double>(n) * n * n);
 }
 
 // ---------------------------------------------------------------------------
@@ -549,15 +729,22 @@ __device__ int keep_count(const T *lam_sorted, int n, int cap, double cutoff, do
   return k;
 }
 
-// Apply the two-branch MPO `spec` on [lo, hi] and recompress sites [a, b]
-// (a <= lo <= hi <= b, the orthogonality centre inside [a, b]).  The centre
-// ends at a and the state is renormalised.
+// Two phases of applying the two-branch MPO `spec` on [lo, hi] and
+// recompressing sites [a, b] (a <= lo <= hi <= b, orthogonality centre inside
+// [a, b]).
+//
+// mps_prepare builds the MPO tensors and runs the left sweep (no truncation
+// yet) and returns the squared norm of the new, untruncated state: for a
+// measurement projector this is the Born probability of the branch, obtained
+// from R factors whose small entries carry absolute (not relative) rounding,
+// so a small probability keeps its relative accuracy (about eps / sqrt(p)).
+// mps_finish then runs the truncating right sweep; the centre ends at a and the
+// state is renormalised.
 template <typename T>
-__device__ void mps_apply_compress(const EngineParams &P, const Smem<T> &S, int64_t shot,
-                                   const Scratch<T> &X, int a, int b) {
+__device__ double mps_prepare(const EngineParams &P, const Smem<T> &S, int64_t shot,
+                              const Scratch<T> &X, int a, int b) {
   const MpoSpec<T> &sp = *S.spec;
   int *chi = S.chi;
-  const int cap = P.chi_cap;
   if (a == b) {
     cplx<T> *A = site_ptr<T>(P, shot, a);
     materialize(sp, S.ppx, S.ppz, a, A, chi[a], chi[a + 1], false, false, X.t);
@@ -565,15 +752,7 @@ __device__ void mps_apply_compress(const EngineParams &P, const Smem<T> &S, int6
     const int64_t tot = static_cast<int64_t>(chi[a]) * 2 * chi[a + 1];
     double nrm = 0;
     for (int64_t e = tid(); e < tot; e += kThreads) nrm += static_cast<double>(cabs2(X.t[e]));
-    nrm = block_sum(nrm, S.red);
-    T inv = static_cast<T>(nrm > 0 ? 1.0 / sqrt(nrm) : 0.0);
-    for (int64_t e = tid(); e < tot; e += kThreads) A[e] = cscale(X.t[e], inv);
-    if (tid() == 0) {
-      if (!(nrm > 0) || !isfinite(nrm)) S.misc[M_FAIL] = STN_ENUMERIC;
-      S.misc[M_CENTER] = a;
-    }
-    __syncthreads();
-    return;
+    return block_sum(nrm, S.red);
   }
   // doubled bond dimensions D[k] for bonds a..b+1
   auto Dbond = [&](int k) { return (k > sp.lo && k <= sp.hi) ? 2 * chi[k] : chi[k]; };
@@ -593,7 +772,7 @@ __device__ void mps_apply_compress(const EngineParams &P, const Smem<T> &S, int6
     if (o > P.ap_elems || g > P.g_elems) S.misc[M_FAIL] = STN_EOVERFLOW;
   }
   __syncthreads();
-  if (S.misc[M_FAIL]) return;
+  if (S.misc[M_FAIL]) return 0.0;
   for (int k = a; k <= b; ++k) {
     bool in = k >= sp.lo && k <= sp.hi;
     bool dl = in && k > sp.lo, dr = in && k < sp.hi;
@@ -608,48 +787,122 @@ __device__ void mps_apply_compress(const EngineParams &P, const Smem<T> &S, int6
   }
   __syncthreads();
   const cplx<T> one = cmake<T>(1, 0), zero = cmake<T>(0, 0);
-  // left sweep: G_{k+1} (bond k+1) for k = a..b-1
+  const int cap = P.chi_cap;
+  (void)cap;
+  // left sweep: R factor of the left part through site k, for k = a..b-1
+  // (R at bond a is the identity: sites left of a are left-canonical).
   for (int k = a; k < b; ++k) {
     const int Dl = Dbond(k), Dr = Dbond(k + 1);
     const cplx<T> *Ak = X.ap + S.off[k - a];
-    cplx<T> *Gout = X.g + S.goff[k + 1 - a];
+    int m;
     if (k == a) {
-      cgemm<T, 1, 0>(Dr, Dr, 2 * Dl, one, Ak, Dr, Ak, Dr, zero, Gout, Dr, S.tile);
+      m = 2 * Dl;
+      const int64_t tot = static_cast<int64_t>(m) * Dr;
+      for (int64_t e = tid(); e < tot; e += kThreads) X.t[e] = Ak[e];
+      __syncthreads();
     } else {
-      const cplx<T> *Gin = X.g + S.goff[k - a];
-      cgemm<T, 0, 0>(Dl, 2 * Dr, Dl, one, Gin, Dl, Ak, 2 * Dr, zero, X.t, 2 * Dr, S.tile);
-      cgemm<T, 1, 0>(Dr, Dr, 2 * Dl, one, Ak, Dr, X.t, Dr, zero, Gout, Dr, S.tile);
+      const int r = S.rdim[k - a];
+      const cplx<T> *Rk = X.g + S.goff[k - a];
+      cgemm<T, 0, 0>(r, 2 * Dr, Dl, one, Rk, Dl, Ak, 2 * Dr, zero, X.t, 2 * Dr, S.tile);
+      if (tid() == 0) S.dmisc[D_FLOPS] += gemm_flops(r, 2 * Dr, Dl);
+      m = 2 * r;
     }
+    if (m > kMaxVec) {
+      if (tid() == 0) S.misc[M_FAIL] = STN_EOVERFLOW;
+      __syncthreads();
+      return 0.0;
+    }
+    qr_r_inplace<T>(m, Dr, X.t, Dr, S.uvec, S.red, S.dmisc + 4);
+    if (tid() == 0) S.dmisc[D_FLOPS] += qr_flops(m, Dr);
+    const int rn = min(m, Dr);
+    cplx<T> *Rout = X.g + S.goff[k + 1 - a];
+    for (int e = tid(); e < rn * Dr; e += kThreads) Rout[e] = X.t[e];
+    if (tid() == 0) S.rdim[k + 1 - a] = rn;
+    __syncthreads();
   }
+  // squared norm: || R_b A'_b ||_F^2 (the right part beyond b is right-canonical)
+  {
+    const int Dl = Dbond(b), n2 = 2 * Dbond(b + 1), r = S.rdim[b - a];
+    cgemm<T, 0, 0>(r, n2, Dl, one, X.g + S.goff[b - a], Dl, X.ap + S.off[b - a], n2, zero, X.y, n2, S.tile);
+    double nrm = 0;
+    for (int e = tid(); e < r * n2; e += kThreads) nrm += static_cast<double>(cabs2(X.y[e]));
+    return block_sum(nrm, S.red);
+  }
+}
+
+template <typename T>
+__device__ void mps_finish(const EngineParams &P, const Smem<T> &S, int64_t shot, const Scratch<T> &X,
+                           int a, int b) {
+  const MpoSpec<T> &sp = *S.spec;
+  int *chi = S.chi;
+  const int cap = P.chi_cap;
+  if (S.misc[M_FAIL]) return;
+  if (a == b) {
+    cplx<T> *A = site_ptr<T>(P, shot, a);
+    const int64_t tot = static_cast<int64_t>(chi[a]) * 2 * chi[a + 1];
+    double nrm = 0;
+    for (int64_t e = tid(); e < tot; e += kThreads) nrm += static_cast<double>(cabs2(X.t[e]));
+    nrm = block_sum(nrm, S.red);
+    T inv = static_cast<T>(nrm > 0 ? 1.0 / sqrt(nrm) : 0.0);
+    for (int64_t e = tid(); e < tot; e += kThreads) A[e] = cscale(X.t[e], inv);
+    if (tid() == 0) {
+      if (!(nrm > 0) || !isfinite(nrm)) S.misc[M_FAIL] = STN_ENUMERIC;
+      S.misc[M_CENTER] = a;
+    }
+    __syncthreads();
+    return;
+  }
+  auto Dbond = [&](int k) { return (k > sp.lo && k <= sp.hi) ? 2 * chi[k] : chi[k]; };
+  const cplx<T> one = cmake<T>(1, 0), zero = cmake<T>(0, 0);
   // right sweep
   int kappa = Dbond(b + 1);
   const cplx<T> *M = X.ap + S.off[b - a];
-  double disc = 0.0;
   for (int k = b; k > a; --k) {
     const int Dl = Dbond(k);
     const int n2 = 2 * kappa;
-    const cplx<T> *Gk = X.g + S.goff[k - a];
-    cgemm<T, 0, 0>(Dl, n2, Dl, one, Gk, Dl, M, n2, zero, X.y, n2, S.tile);
-    // H = M^dag Y (n2 x n2)
-    const int NS = JacobiSmem<T>::n;
-    const bool in_smem = n2 <= NS;
-    cplx<T> *H = in_smem ? S.jA : X.h;
-    cplx<T> *V = in_smem ? S.jV : X.v;
-    const int ldh = n2;
-    cgemm<T, 1, 0>(n2, n2, Dl, one, M, n2, X.y, n2, zero, H, ldh, S.tile);
-    if (n2 > 2 * kMaxPairs) {
-      if (tid() == 0) S.misc[M_FAIL] = STN_EOVERFLOW;
-      __syncthreads();
-      return;
-    }
-    jacobi_heev<T>(n2, H, ldh, V, n2, S.rp, &S.misc[M_JFLAG], S.red);
-    for (int i = tid(); i < n2; i += kThreads) {
-      T l = H[i * ldh + i].re;
-      if (!isfinite(static_cast<double>(l))) {
-        S.misc[M_FAIL] = STN_ENUMERIC;
-        l = T(0);
+    const int r = S.rdim[k - a];
+    const cplx<T> *Rk = X.g + S.goff[k - a];
+    // C = R_k M (r x n2), then its SVD
+    cgemm<T, 0, 0>(r, n2, Dl, one, Rk, Dl, M, n2, zero, X.y, n2, S.tile);
+    const bool in_smem = r * n2 + n2 * n2 <= P.svd_elems;
+    cplx<T> *Cc = in_smem ? S.jbuf : X.h;
+    cplx<T> *Vc = in_smem ? S.jbuf + r * n2 : X.v;
+    // In the complex64 path a bond whose SVD fits shared memory in complex128
+    // is decomposed in double precision: FP32 Jacobi rotations leave the small
+    // singular directions with an absolute error of about sqrt(#rotations)
+    // eps sigma_1, which would be dropped or kept wrongly at every sweep.
+    bool svd64 = false;
+    if constexpr (sizeof(T) == 4) svd64 = 2 * (r * n2 + n2 * n2) <= P.svd_elems;
+    if (svd64) {
+      cplx<double> *Cd = reinterpret_cast<cplx<double> *>(S.jbuf), *Vd = Cd + r * n2;
+      double *sd = reinterpret_cast<double *>(X.te);
+      for (int e = tid(); e < r * n2; e += kThreads) {
+        int i = e / n2, j = e % n2;
+        cplx<T> v = X.y[e];
+        Cd[j * r + i] = cmake<double>(static_cast<double>(v.re), static_cast<double>(v.im));
       }
-      X.lam[i] = l;
+      __syncthreads();
+      svd_onesided<double>(r, n2, Cd, Vd, sd, &S.misc[M_JFLAG], S.red);
+      for (int e = tid(); e < n2 * n2; e += kThreads)
+        X.v[e] = cmake<T>(static_cast<T>(Vd[e].re), static_cast<T>(Vd[e].im));
+      for (int i = tid(); i < n2; i += kThreads) X.lam[i] = static_cast<T>(sd[i]);
+      __syncthreads();
+      Vc = X.v;
+    } else {
+      for (int e = tid(); e < r * n2; e += kThreads) {
+        int i = e / n2, j = e % n2;
+        Cc[j * r + i] = X.y[e];
+      }
+      __syncthreads();
+      if (in_smem) svd_onesided<T>(r, n2, Cc, Vc, X.lam, &S.misc[M_JFLAG], S.red);
+      else svd_onesided_blocked<T>(r, n2, Cc, Vc, X.lam, &S.misc[M_JFLAG], S.red, S.jbuf, P.svd_elems);
+    }
+    if (tid() == 0) S.dmisc[D_FLOPS] += gemm_flops(r, n2, Dl) + svd_flops(r, n2);
+    for (int i = tid(); i < n2; i += kThreads) {
+      if (!isfinite(static_cast<double>(X.lam[i]))) {
+        S.misc[M_FAIL] = STN_ENUMERIC;
+        X.lam[i] = T(0);
+      }
     }
     __syncthreads();
     if (S.misc[M_FAIL]) return;
@@ -671,12 +924,13 @@ __device__ void mps_apply_compress(const EngineParams &P, const Smem<T> &S, int6
     }
     __syncthreads();
     const int keep = S.misc[M_KEEP];
-    // sorted, kept eigenvectors: Vs[:, c] = V[:, perm[c]], c < keep
+    // sorted, kept right singular vectors: Vs[:, c] = V[:, perm[c]], c < keep
     for (int e = tid(); e < n2 * keep; e += kThreads) {
       int i = e / keep, c = e % keep;
-      X.vs[i * keep + c] = V[i * n2 + S.perm[c]];
+      X.vs[i * keep + c] = Vc[static_cast<int64_t>(S.perm[c]) * n2 + i];
     }
     __syncthreads();
+    reorthonormalize<T>(n2, keep, X.vs, X.e, X.y, S.tile);
     // new right-canonical site k: B[c][s][r] = conj(Vs[(s*kappa + r)][c])
     cplx<T> *Bk = site_ptr<T>(P, shot, k);
     for (int e = tid(); e < keep * n2; e += kThreads) {
@@ -689,7 +943,10 @@ __device__ void mps_apply_compress(const EngineParams &P, const Smem<T> &S, int6
     const int Dll = Dbond(k - 1);
     const cplx<T> *Akm1 = X.ap + S.off[k - 1 - a];
     cgemm<T, 0, 0>(2 * Dll, keep, Dl, one, Akm1, Dl, X.w, keep, zero, X.mbuf, keep, S.tile);
-    if (tid() == 0) chi[k] = keep;
+    if (tid() == 0) {
+      chi[k] = keep;
+      S.dmisc[D_FLOPS] += gemm_flops(Dl, keep, n2) + gemm_flops(2 * Dll, keep, Dl);
+    }
     __syncthreads();
     M = X.mbuf;
     kappa = keep;
@@ -710,7 +967,13 @@ __device__ void mps_apply_compress(const EngineParams &P, const Smem<T> &S, int6
     S.misc[M_MAXCHI] = mx;
   }
   __syncthreads();
-  (void)disc;
+}
+
+template <typename T>
+__device__ void mps_apply_compress(const EngineParams &P, const Smem<T> &S, int64_t shot,
+                                   const Scratch<T> &X, int a, int b) {
+  mps_prepare<T>(P, S, shot, X, a, b);
+  mps_finish<T>(P, S, shot, X, a, b);
 }
 
 // <phi| i^m X^x Z^z |phi> over sites [a, b] (centre inside, so the rest of
@@ -741,9 +1004,11 @@ __device__ double mps_expect(const EngineParams &P, const Smem<T> &S, int64_t sh
     __syncthreads();
     if (k == a) {
       cgemm<T, 1, 0>(cr, cr, 2 * cl, one, A, cr, X.sa, cr, zero, X.e, cr, S.tile);
+      if (tid() == 0) S.dmisc[D_FLOPS] += gemm_flops(cr, cr, 2 * cl);
     } else {
       cgemm<T, 0, 0>(cl, 2 * cr, cl, one, X.e, cl, X.sa, 2 * cr, zero, X.te, 2 * cr, S.tile);
       cgemm<T, 1, 0>(cr, cr, 2 * cl, one, A, cr, X.te, cr, zero, X.e, cr, S.tile);
+      if (tid() == 0) S.dmisc[D_FLOPS] += gemm_flops(cl, 2 * cr, cl) + gemm_flops(cr, cr, 2 * cl);
     }
   }
   const int cb = chi[b + 1];
@@ -854,12 +1119,42 @@ __device__ void tableau_caseB(uint64_t *tx, uint64_t *tz, uint8_t *tm, int n, in
   __syncthreads();
 }
 
+// Projector MPO of outcome `bit` for the measured P' (thread 0): case A
+// (no X or Y in P') projects with (I + (-1)^bit P')/2; case B applies the
+// controlled-Pauli product with the site-j projection onto the lambda
+// eigenvector, lambda = (-1)^bit * sign(P').
+template <typename T>
+__device__ void set_meas_spec(const Smem<T> &S, int bit) {
+  MpoSpec<T> &sp = *S.spec;
+  const int mb = S.misc[M_BIT];
+  const int m = mb & 3;
+  const int neg = (mb >> 4) & 1;
+  if (!S.misc[M_CASEB]) {
+    sp.kind = MPO_PROJ_Z;
+    sp.w0 = cmake<T>(T(0.5), 0);
+    cplx<T> w1 = ipow<T>(m);
+    T sgn = bit ? T(-0.5) : T(0.5);
+    sp.w1 = cmake<T>(w1.re * sgn, w1.im * sgn);
+  } else {
+    const int jq = S.misc[M_J];
+    const bool zj = (S.ppz[jq >> 6] >> (jq & 63)) & 1;
+    int lam = (bit ? -1 : 1) * (neg ? -1 : 1);
+    const T r2 = static_cast<T>(0.70710678118654752440);
+    sp.kind = MPO_PROJ_B;
+    sp.w0 = cmake<T>(1, 0);
+    sp.w1 = cmake<T>(1, 0);
+    sp.v0 = cmake<T>(r2, 0);
+    sp.v1 = zj ? cmake<T>(0, lam > 0 ? r2 : -r2) : cmake<T>(lam > 0 ? r2 : -r2, 0);
+    S.misc[M_LIDX] = (zj ? 2 : 0) + (lam < 0 ? 1 : 0);
+  }
+}
+
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
   extern __shared__ __align__(16) char smem_raw[];
   const int n = P.n, W = P.W;
-  Smem<T> S = carve<T>(smem_raw, n, W);
+  Smem<T> S = carve<T>(smem_raw, n, W, P.svd_elems);
   Scratch<T> X = scratch_for<T>(P, P.work_c);
   for (int64_t shot = blockIdx.x; shot < P.shots; shot += gridDim.x) {
     // load the frame and the MPS bookkeeping
@@ -875,6 +1170,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
       S.misc[M_MAXCHI] = P.maxchi[shot];
       S.dmisc[D_DISC] = P.disc[shot];
       S.dmisc[D_LOGP] = P.logp[shot];
+      S.dmisc[D_FLOPS] = 0.0;
     }
     __syncthreads();
     const uint64_t gshot = P.shot_offset + static_cast<uint64_t>(shot);
@@ -964,10 +1260,17 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
           const int a = S.misc[M_A], b = S.misc[M_B];
           int caseB = 0, lidx = 0, outcome = 0;
           if (meas) {
+            // The Born probability of the less likely branch is taken from the
+            // norm of its projected state (accurate for small p); the FP32
+            // expectation value only decides which branch that is.
             const int mb = S.misc[M_BIT];
             double e = mps_expect<T>(P, S, shot, X, a, b, mb & 3);
+            const int small = e >= 0.0 ? 1 : 0;
+            if (tid() == 0) set_meas_spec<T>(S, small);
+            __syncthreads();
+            double ps = fmin(1.0, fmax(0.0, mps_prepare<T>(P, S, shot, X, a, b)));
             if (tid() == 0) {
-              double p0 = fmin(1.0, fmax(0.0, 0.5 * (1.0 + e)));
+              double p0 = small == 0 ? ps : 1.0 - ps;
               double u = philox_uniform(P.seed, gshot, op.ev);
               int bit = u < p0 ? 0 : 1;
               double pb = bit == 0 ? p0 : 1.0 - p0;
@@ -976,36 +1279,18 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
               S.dmisc[D_LOGP] += log(pb);
               int flip = philox_uniform(P.seed, gshot, op.ev + 1) < P.pM ? 1 : 0;
               if (bit ^ flip) P.records[shot * P.rec_bytes + op.idx / 8] |= static_cast<uint8_t>(1u << (op.idx % 8));
-              MpoSpec<T> &sp = *S.spec;
-              const int m = mb & 3;
-              const int neg = (mb >> 4) & 1;
-              if (!S.misc[M_CASEB]) {
-                sp.kind = MPO_PROJ_Z;
-                sp.w0 = cmake<T>(T(0.5), 0);
-                cplx<T> w1 = ipow<T>(m);
-                T sgn = bit ? T(-0.5) : T(0.5);
-                sp.w1 = cmake<T>(w1.re * sgn, w1.im * sgn);
-              } else {
-                const int jq = S.misc[M_J];
-                const bool zj = (S.ppz[jq >> 6] >> (jq & 63)) & 1;
-                int lam = (bit ? -1 : 1) * (neg ? -1 : 1);
-                int li = (zj ? 2 : 0) + (lam < 0 ? 1 : 0);
-                const T r2 = static_cast<T>(0.70710678118654752440);
-                sp.kind = MPO_PROJ_B;
-                sp.w0 = cmake<T>(1, 0);
-                sp.w1 = cmake<T>(1, 0);
-                sp.v0 = cmake<T>(r2, 0);
-                sp.v1 = zj ? cmake<T>(0, lam > 0 ? r2 : -r2) : cmake<T>(lam > 0 ? r2 : -r2, 0);
-                S.misc[M_LIDX] = li;
-              }
               S.misc[M_OUTCOME] = bit;
+              if (bit != small) set_meas_spec<T>(S, bit);
             }
             __syncthreads();
             caseB = S.misc[M_CASEB];
             lidx = S.misc[M_LIDX];
             outcome = S.misc[M_OUTCOME];
+            if (outcome != small) mps_prepare<T>(P, S, shot, X, a, b);
+            mps_finish<T>(P, S, shot, X, a, b);
+          } else {
+            mps_apply_compress<T>(P, S, shot, X, a, b);
           }
-          mps_apply_compress<T>(P, S, shot, X, a, b);
           if (meas) {
             if (caseB) tableau_caseB(S.tx, S.tz, S.tm, n, W, S.ppx, S.ppz, S.misc[M_J], lidx);
             if (tid() == 0 && op.pauli == 1) {
@@ -1033,6 +1318,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
       P.maxchi[shot] = S.misc[M_MAXCHI];
       P.disc[shot] = S.dmisc[D_DISC];
       P.logp[shot] = S.dmisc[D_LOGP];
+      P.flops[shot] += S.dmisc[D_FLOPS];
       if (S.misc[M_FAIL]) atomicCAS(P.err, 0, S.misc[M_FAIL]);
     }
     __syncthreads();
@@ -1072,6 +1358,58 @@ __global__ void init_kernel(EngineParams P) {
 }
 
 // ---------------------------------------------------------------------------
+// Kernel-level checks of the dense routines on one CTA (complex elements of
+// precision T, column-major C/V for the SVD, row-major B for the QR).
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1) dense_check_kernel(int what, int m, int n, cplx<T> *A,
+                                                                  cplx<T> *V, T *sig2, int use_smem) {
+  extern __shared__ __align__(16) char smem_raw[];
+  double *red = reinterpret_cast<double *>(smem_raw);
+  double *dm = red + kThreads;
+  int *flag = reinterpret_cast<int *>(dm + 16);
+  cplx<T> *uv = reinterpret_cast<cplx<T> *>(flag + 16);
+  cplx<T> *buf = uv + kMaxVec;
+  if (what == 0) {
+    qr_r_inplace<T>(m, n, A, n, uv, red, dm);
+  } else {
+    cplx<T> *C = A, *VV = V;
+    if (use_smem == 1) {
+      C = buf;
+      VV = buf + m * n;
+      for (int e = tid(); e < m * n; e += kThreads) C[e] = A[e];
+      __syncthreads();
+    }
+    if (use_smem == 2) svd_onesided_blocked<T>(m, n, C, VV, sig2, flag, red, buf, SvdSmem<T>::elems);
+    else svd_onesided<T>(m, n, C, VV, sig2, flag, red);
+    if (use_smem == 1) {
+      for (int e = tid(); e < m * n; e += kThreads) A[e] = C[e];
+      for (int e = tid(); e < n * n; e += kThreads) V[e] = VV[e];
+    }
+  }
+}
+
+template <typename T>
+static cudaError_t launch_dense_check_t(int what, int m, int n, void *A, void *V, void *sig2, int use_smem,
+                                        cudaStream_t s) {
+  size_t smem = sizeof(double) * (kThreads + 16) + sizeof(int) * 16 + sizeof(cplx<T>) * kMaxVec;
+  if (use_smem) smem += sizeof(cplx<T>) * SvdSmem<T>::elems;  // 1: matrix in smem, 2: blocked
+  cudaError_t e = cudaFuncSetAttribute(dense_check_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  dense_check_kernel<T><<<1, kThreads, smem, s>>>(what, m, n, static_cast<cplx<T> *>(A),
+                                                  static_cast<cplx<T> *>(V), static_cast<T *>(sig2), use_smem);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_check(int precision, int what, int m, int n, void *A, void *V, void *sig2,
+                               int use_smem, cudaStream_t s) {
+  return precision == 0 ? launch_dense_check_t<double>(what, m, n, A, V, sig2, use_smem, s)
+                        : launch_dense_check_t<float>(what, m, n, A, V, sig2, use_smem, s);
+}
+
+int svd_smem_elems(int precision) { return precision == 0 ? SvdSmem<double>::elems : SvdSmem<float>::elems; }
+
+// ---------------------------------------------------------------------------
 // host side
 ScratchPlan plan_scratch(int n, const int *chimax, int chi_cap) {
   ScratchPlan p{};
@@ -1090,12 +1428,27 @@ ScratchPlan plan_scratch(int n, const int *chimax, int chi_cap) {
   return p;
 }
 
-size_t round_kernel_smem(int precision, int n, int W) {
-  return precision == 0 ? smem_bytes<double>(n, W) : smem_bytes<float>(n, W);
+// Largest SVD buffer (complex elements, at most SvdSmem) that keeps the round
+// kernel within the 227 KB of shared memory a CTA may use.
+template <typename T>
+static int svd_elems_for(int n, int W) {
+  const size_t limit = 227 * 1024;
+  size_t base = smem_bytes<T>(n, W, 0);
+  if (base + 64 >= limit) return 0;
+  size_t e = (limit - base - 64) / sizeof(cplx<T>);
+  return static_cast<int>(e < static_cast<size_t>(SvdSmem<T>::elems) ? e : SvdSmem<T>::elems);
+}
+
+int round_kernel_svd_elems(int precision, int n, int W) {
+  return precision == 0 ? svd_elems_for<double>(n, W) : svd_elems_for<float>(n, W);
+}
+
+size_t round_kernel_smem(int precision, int n, int W, int svd_elems) {
+  return precision == 0 ? smem_bytes<double>(n, W, svd_elems) : smem_bytes<float>(n, W, svd_elems);
 }
 
 int jacobi_smem_limit(int precision) {
-  return precision == 0 ? JacobiSmem<double>::n : JacobiSmem<float>::n;
+  return precision == 0 ? SvdSmem<double>::elems : SvdSmem<float>::elems;
 }
 
 template <typename T>
@@ -1112,7 +1465,7 @@ cudaError_t launch_init(int precision, const EngineParams &p, cudaStream_t s) {
 
 template <typename T>
 static cudaError_t launch_round_t(const EngineParams &p, int grid, cudaStream_t s) {
-  size_t smem = smem_bytes<T>(p.n, p.W);
+  size_t smem = smem_bytes<T>(p.n, p.W, p.svd_elems);
   cudaError_t e = cudaFuncSetAttribute(round_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;

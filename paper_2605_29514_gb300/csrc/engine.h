@@ -37,10 +37,12 @@ struct EngineParams {
   int *maxchi, *near, *status;  // [shot]
   uint8_t *records;         // [shot][rec_bytes]
   double *born;             // [shot][n_meas]
+  double *flops;            // [shot] algorithmic FLOPs, cumulative over batches
   // per-CTA scratch, complex elements of the path's precision
   void *scratch;
   int64_t scratch_elems, ap_elems, g_elems;
   int work_c;               // largest bond of the plan (sizes the work area)
+  int svd_elems;            // complex elements of the shared-memory SVD buffer
   int *err;                 // first error code seen on the device
 };
 
@@ -50,11 +52,15 @@ struct ScratchPlan {
 };
 
 ScratchPlan plan_scratch(int n, const int *chimax, int chi_cap);
-size_t round_kernel_smem(int precision, int n, int W);
+size_t round_kernel_smem(int precision, int n, int W, int svd_elems);
+int round_kernel_svd_elems(int precision, int n, int W);
 int jacobi_smem_limit(int precision);
 
 cudaError_t launch_init(int precision, const EngineParams &p, cudaStream_t s);
 cudaError_t launch_round(int precision, const EngineParams &p, int grid, cudaStream_t s);
+cudaError_t launch_dense_check(int precision, int what, int m, int n, void *A, void *V, void *sig2,
+                               int use_smem, cudaStream_t s);
+int svd_smem_elems(int precision);
 cudaError_t launch_philox(uint64_t seed, uint64_t shot_offset, int64_t n_shots,
                           uint32_t event_offset, int n_events, double *out, cudaStream_t s);
 

@@ -143,7 +143,8 @@ def test_d3_truncating_cap_and_xx_pairs():
 
 def test_d3_complex64_parity():
     """The complex64 path on the d=3 workload: Born within 1e-5 relative."""
-    w = D3_EXACT.with_(precision=PRECISION_C64, svd_cutoff=1e-3, degeneracy_tol=1e-4)
+    w = D3_EXACT.with_(precision=PRECISION_C64, svd_cutoff=D5_BENCH.svd_cutoff,
+                       degeneracy_tol=D5_BENCH.degeneracy_tol)
     shots = 24
     sim, out, theta = gpu_run(w, shots)
     prog = make_program(w)
