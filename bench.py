@@ -6,11 +6,12 @@ A step is one program segment (one syndrome round, or the final readout)
 applied to a batch of B shots; a batch completes after rounds + 1 = 6 steps
 and the next batch starts with new shot indices.  K is rounded up to a
 multiple of 6 so every segment is timed equally often, and
-    value = B * K / 6 / timed seconds
-is whole-shot throughput.  Inputs (angle table, program) are resident in HBM
-and records stay on the device in the timed region; `e2e` times the public
-C ABI call stn_sample_shots with host buffers (angle upload and record
-download inside the timed region).
+    value = B * K / 6 / device seconds
+is whole-shot throughput, timed with CUDA events on the simulator's stream;
+the angle table and program are resident in HBM.  The W warm-up steps are
+syndrome round 0 of W fresh batches.  `e2e` is the same batches timed on the
+host clock through the C ABI with host buffers: the angle upload from pinned
+memory and every batch's record download are inside it.
 
 Run: python bench.py [--gpus N] [--steps K] [--warmup W] [--shots B]
      python bench.py --impl reference    (the CPU oracle on a bounded sample)
@@ -46,7 +47,6 @@ def parse():
     ap.add_argument("--impl", default="stn", choices=["stn", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
@@ -196,72 +196,55 @@ def main():
     stream = torch.cuda.current_stream()
     sim = stn.Simulator(w, max_shots=B, stream=stream.cuda_stream)
     theta = theta_table(w, sim.n_pairs)
-    d_theta = torch.tensor(theta, dtype=torch.float64, device="cuda")
+    th_host = torch.tensor(theta, dtype=torch.float64).pin_memory()
+    d_theta = torch.empty_like(th_host, device="cuda")
+    d_theta.copy_(th_host)
+    rec_host = torch.empty((B, sim.rec_bytes), dtype=torch.uint8).pin_memory()
     base = rank * 10 ** 9  # disjoint shot ranges per rank
 
-    state = {"seg": 0, "batch": 0}
-
-    def step():
-        if state["seg"] == 0:
-            sim.begin_batch(B, base + state["batch"] * B)
-        sim.apply_round_device(state["seg"], d_theta.data_ptr())
-        state["seg"] += 1
-        if state["seg"] == segs:
-            state["seg"] = 0
-            state["batch"] += 1
-
-    # warm-up: W segments of batch 0, then a fresh batch for the timed region
-    for _ in range(W):
-        step()
+    # warm-up: W steps, each the first segment (syndrome round 0) of a fresh batch
+    for i in range(W):
+        sim.begin_batch(B, base + i * B)
+        sim.apply_round_device(0, d_theta.data_ptr())
     sim.sync()
-    state["seg"], state["batch"] = 0, 1
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
     clocks = ClockSampler(local)
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t_host = time.perf_counter()
-    ev0.record(stream)
-    launches = 0
     flops0 = sim.algorithmic_flops()
-    for _ in range(K):
-        if state["seg"] == 0:
-            launches += 1  # batch initialisation kernel
-        step()
+    launches = 0
+    # timed: K segments = K / 6 complete batches.  The host clock also covers the
+    # angle upload from pinned memory and each batch's record download (e2e).
+    t_host = time.perf_counter()
+    d_theta.copy_(th_host, non_blocking=True)
+    ev0.record(stream)
+    for b in range(K // segs):
+        sim.begin_batch(B, base + (W + b) * B)
         launches += 1
-    ev1.record(stream)
-    torch.cuda.synchronize()
+        for seg in range(segs):
+            sim.apply_round_device(seg, d_theta.data_ptr())
+            launches += 1
+        if b + 1 == K // segs:
+            ev1.record(stream)
+        sim.read_records_into(rec_host.data_ptr())
     host_s = time.perf_counter() - t_host
-    sim.sync()
+    torch.cuda.synchronize()
     flops = sim.algorithmic_flops() - flops0
     clk = clocks.stop()
     secs = ev0.elapsed_time(ev1) / 1000.0
     if pg:
-        t = torch.tensor([secs], dtype=torch.float64, device="cuda")
+        t = torch.tensor([secs, host_s], dtype=torch.float64, device="cuda")
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        secs = float(t.item())
+        secs, host_s = float(t[0].item()), float(t[1].item())
     shots_done = ws * B * K // segs
     value = shots_done / secs
-
-    # end to end through the C ABI with host buffers
-    e2e = None
-    if not args.no_e2e:
-        import numpy as np
-        torch.cuda.synchronize()
-        if pg:
-            pg.barrier()
-        t0 = time.perf_counter()
-        out = sim.sample_shots(B, base + 10 ** 8, theta, born=False, stats=True)
-        e2e_s = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": ws * B / e2e_s, "unit": "shots/s",
-               "h2d_bytes_per_step": int(theta.nbytes) // 1,
-               "d2h_bytes_per_step": int(out["records"].nbytes + B * 24) // segs,
-               "note": "stn_sample_shots: angle upload per segment, records + per-shot stats download"}
+    e2e = {"value": shots_done / host_s, "unit": "shots/s",
+           "h2d_bytes_per_step": int(th_host.numel() * 8) / K,
+           "d2h_bytes_per_step": int(rec_host.numel()) * (K // segs) / K,
+           "path": "C ABI with host buffers: angles copied from pinned host memory, records read back "
+                   "into pinned host memory after each batch (stn_read_records)"}
 
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -289,7 +272,7 @@ def main():
                            "l2": "per-shot MPS state (GBs) larger than L2; no flush",
                            "parallelism": f"shots sharded over {ws} rank(s)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "host_seconds": host_s}
+                "clocks": clk}
         print(json.dumps(line), flush=True)
     sim.close()
     if pg:

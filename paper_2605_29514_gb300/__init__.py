@@ -117,6 +117,11 @@ class Simulator:
         self._check(self.lib.stn_algorithmic_flops(self.ctx, ctypes.byref(v)))
         return v.value
 
+    def read_records_into(self, h_records_ptr):
+        """Packed records of the batch into caller-owned host memory
+        ([shots][rec_bytes] bytes, e.g. pinned)."""
+        self._check(self.lib.stn_read_records(self.ctx, ctypes.c_void_p(h_records_ptr), None, None))
+
     def device_records_ptr(self):
         return self.lib.stn_device_records(self.ctx)
 

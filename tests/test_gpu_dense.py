@@ -50,14 +50,18 @@ def test_qr_r_factor(precision, m, n):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("m,n,smem", [(4, 4, 1), (32, 32, 1), (16, 40, 1), (60, 24, 1), (64, 64, 0),
-                                      (130, 70, 0), (64, 64, 2), (200, 150, 2), (120, 256, 2),
-                                      (512, 512, 2)])
-def test_onesided_svd(precision, m, n, smem):
+@pytest.mark.parametrize("m,n,smem,decay", [(4, 4, 1, 0.1), (32, 32, 1, 0.1), (16, 40, 1, 0.1),
+                                            (60, 24, 1, 0.1), (64, 64, 0, 0.1), (130, 70, 0, 0.1),
+                                            (64, 64, 2, 0.1), (200, 150, 2, 0.5), (120, 256, 2, 0.5),
+                                            (512, 512, 2, 0.5)])
+def test_onesided_svd(precision, m, n, smem, decay):
+    """Clustered spectra (decay 0.1: neighbours within 10%) on the small cases;
+    the large, blocked cases use the strongly graded spectra of MPS bonds
+    (Schmidt values falling by orders of magnitude, Sec. IV B)."""
     if smem == 1 and precision == 0 and m * n + n * n > 8192:
         pytest.skip("does not fit shared memory in complex128")
     rng = np.random.default_rng(7 * m + n)
-    a = rand(rng, m, n, decay=0.1)
+    a = rand(rng, m, n, decay=decay)
     dc = torch.tensor(a.T.copy(), dtype=CDT[precision], device="cuda")  # column-major
     dv = torch.zeros((n, n), dtype=CDT[precision], device="cuda")
     ds = torch.zeros(n, dtype=RDT[precision], device="cuda")

@@ -169,8 +169,10 @@ def test_d5_first_round_parity():
     na = 24
     for s in range(shots):
         ref = run_shot(w1, s, theta, prog1)
-        bits = out["bits"][s][:na]
-        assert list(bits) == ref.record[:na] or out["near_draws"][s] > 0 or ref.near_draws > 0
-        rb = np.array(ref.born[:na])
-        err = np.abs(out["born"][s][:na] - rb) / np.maximum(rb, 1e-4)
-        assert np.all(err < 1e-5)
+        bits = list(out["bits"][s][:na])
+        upto = next((i for i in range(na) if bits[i] != ref.record[i]), na)
+        if upto < na:  # only after a draw within 1e-5 of its threshold
+            assert out["near_draws"][s] > 0 or ref.near_draws > 0, f"shot {s}: record {upto} differs"
+        rb = np.array(ref.born[:upto])
+        err = np.abs(out["born"][s][:upto] - rb) / np.maximum(rb, 1e-4)
+        assert np.all(err < 1e-5), f"shot {s}: max rel Born error {err.max():.3e} at record {int(err.argmax())}"
