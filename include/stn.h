@@ -184,7 +184,13 @@ stn_status stn_philox_uniforms(uint64_t seed, uint64_t shot_offset, int64_t n_sh
  *   vectors, d_sig2[n] (real, of the precision) sigma^2, unsorted.
  *   in_shared = 1 runs it in shared memory (requires m n + n^2 to fit);
  *   in_shared = 2 runs the blocked variant (column-block pairs in shared
- *   memory, C and V in global memory), the one used for large bonds.
+ *   memory, C and V in global memory).
+ *   in_shared = 3 runs the large-bond path of the truncation sweep instead:
+ *   d_c is then ROW-major m x n (m <= 1024) and is overwritten; its
+ *   Householder R factor is formed and one-sided Jacobi runs on R^dag, so
+ *   column c < min(m,n) of d_v is the right singular vector (the normalised
+ *   rotated column of R^dag) for sigma_c^2 = d_sig2[c]; later columns and
+ *   entries are zero.
  * Errors: STN_EINVAL on bad sizes, STN_ECUDA on launch failure. */
 stn_status stn_dense_qr(int32_t precision, int32_t m, int32_t n, void *d_b, void *cuda_stream);
 stn_status stn_dense_svd(int32_t precision, int32_t m, int32_t n, void *d_c, void *d_v, void *d_sig2,

@@ -430,8 +430,9 @@ stn_status stn_dense_svd(int32_t precision, int32_t m, int32_t n, void *d_c, voi
   if ((precision != 0 && precision != 1) || m < 1 || n < 1 || n > 512 || !d_c || !d_v || !d_sig2)
     return STN_EINVAL;
   if (in_shared == 1 && m * n + n * n > stn::svd_smem_elems(precision)) return STN_EINVAL;
-  if (in_shared < 0 || in_shared > 2 || (in_shared == 2 && 2 * m + 4 > stn::svd_smem_elems(precision)))
+  if (in_shared < 0 || in_shared > 3 || (in_shared >= 2 && 2 * m + 4 > stn::svd_smem_elems(precision)))
     return STN_EINVAL;
+  if (in_shared == 3 && (m > 1024 || 2 * n + 4 > stn::svd_smem_elems(precision))) return STN_EINVAL;
   cudaError_t e = stn::launch_dense_check(precision, 1, m, n, d_c, d_v, d_sig2, in_shared,
                                           static_cast<cudaStream_t>(cuda_stream));
   return e == cudaSuccess ? STN_OK : STN_ECUDA;

@@ -4,18 +4,21 @@
 // (one syndrome round).  Clifford gates and Pauli noise update the inverse
 // tableau held in shared memory (bit-exact integer row operations, Sec. IV A).
 // A crosstalk rotation or a measurement pushes its Pauli through the tableau
-// and acts on the shot's MPS as a bond-2 Pauli-string MPO; the MPS is then
-// recompressed (Sec. IV B, Eq. 8) by a Gram-matrix sweep:
-//   left sweep   G_{k+1} = sum_s A'^s_k^dag G_k A'^s_k      (left Gram of the
-//                doubled state, G_a = identity since sites < a are
-//                left-canonical)
-//   right sweep  H = M_k^dag G_k M_k, H = V diag(lambda) V^dag; the kept
-//                columns of V give the new right-canonical site, and
-//                M_{k-1} = A'_{k-1} (M_k V) carries the rest to the left.
-// The eigenvalues of H are the squared Schmidt values of the bond, so keeping
-// the largest ones is the truncation of Eq. 8.  Dense work runs in complex
-// T (float or double); norms, Born probabilities and log-probabilities in
-// double.
+// and acts on the shot's MPS as a bond-2 Pauli-string MPO; the touched span
+// is then recompressed (Sec. IV B, Eq. 8) by a two-pass sweep:
+//   left sweep   R_{k+1} = R factor of (R_k A'_k), R_a = identity since the
+//                sites left of the span are left-canonical (Householder QR,
+//                no Q formed); ||R_b A'_b||^2 is the squared norm of the new
+//                state, which for a projector is the Born probability;
+//   right sweep  C = R_k M_k = U Sigma V^dag (one-sided Jacobi); the kept
+//                columns of V give the new right-canonical site and
+//                M_{k-1} = A'_{k-1} (M_k V_keep) carries the rest to the left.
+// Sigma holds the Schmidt values of the bond, so keeping the largest ones is
+// the truncation of Eq. 8.  Small bonds are decomposed in shared memory (in
+// double precision on the complex64 path where that fits); large bonds take
+// the Householder R factor of C and run Jacobi on its conjugate transpose,
+// which converges in a few sweeps.  Dense work runs in complex T (float or
+// double); norms, Born probabilities and log-probabilities in double.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -238,54 +241,156 @@ __device__ __forceinline__ T warp_sum(T v) {
 // Householder QR of B (m x n, row-major, leading dimension ld), in place: on
 // return rows 0..min(m,n)-1 hold R (upper trapezoidal) and the rest is zero.
 // Each step uses the Hermitian reflector P = I - 2 u u^dag with
-// P x = gamma e_1, gamma = -(x_0/|x_0|) ||x||.  CTA-wide; u lives in `uv`.
+// P x = gamma e_1, gamma = -(x_0/|x_0|) ||x||.  Blocked by panels of nb
+// columns: a panel is copied to shared memory (pbuf) and factored there,
+// its reflectors u_1..u_nb are kept as the columns of V, and the product
+// P_nb ... P_1 = I - V T^dag V^dag (compact WY form, T upper triangular with
+// T_kk = 2, T[0:k, k] = -2 T[0:k, 0:k] V[:, 0:k]^dag u_k) is applied to the
+// trailing columns at once, one thread per column, so the trailing matrix is
+// read and written twice per panel rather than per column.  pbuf needs
+// m nb + 2 nb^2 complex elements (nb is reduced to fit).  CTA-wide.
+constexpr int kQrPanel = 16;
+
 template <typename T>
-__device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *uv, double *red,
+__device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *pbuf, int pbuf_elems, double *red,
                              double *dm) {
   const int steps = min(m, n);
-  for (int j = 0; j < steps; ++j) {
-    double nx2 = 0;
-    for (int i = j + tid(); i < m; i += kThreads) nx2 += static_cast<double>(cabs2(B[static_cast<int64_t>(i) * ld + j]));
-    nx2 = block_sum(nx2, red);
-    if (!(nx2 > 0.0)) continue;  // zero column: R row j is already final
+  int nb = kQrPanel;
+  while (nb > 1 && static_cast<int64_t>(m) * nb + 2 * nb * nb > pbuf_elems) --nb;
+  cplx<T> *Vp = pbuf;                                   // [(m - j0)][nb], row-major
+  cplx<T> *Tm = pbuf + static_cast<int64_t>(m) * nb;  // [nb][nb]
+  cplx<T> *G = Tm + nb * nb;                            // [nb][nb], G[a][b] = u_a^dag u_b
+  for (int j0 = 0; j0 < steps; j0 += nb) {
+    const int jb = min(nb, steps - j0);
+    const int mr = m - j0;
+    for (int e = tid(); e < mr * jb; e += kThreads) {
+      const int i = e / jb, c = e % jb;
+      Vp[i * nb + c] = B[static_cast<int64_t>(j0 + i) * ld + j0 + c];
+    }
+    __syncthreads();
+    for (int jj = 0; jj < jb; ++jj) {
+      double nx2 = 0;
+      for (int i = jj + tid(); i < mr; i += kThreads) nx2 += static_cast<double>(cabs2(Vp[i * nb + jj]));
+      nx2 = block_sum(nx2, red);
+      // rows above the diagonal of this column are final R entries
+      for (int i = tid(); i < jj; i += kThreads) B[static_cast<int64_t>(j0 + i) * ld + j0 + jj] = Vp[i * nb + jj];
+      if (!(nx2 > 0.0)) {  // zero column: no reflector, R row jj is final
+        for (int i = tid(); i < mr; i += kThreads) {
+          if (i >= jj) B[static_cast<int64_t>(j0 + i) * ld + j0 + jj] = cmake<T>(0, 0);
+          Vp[i * nb + jj] = cmake<T>(0, 0);
+        }
+        __syncthreads();
+        continue;
+      }
+      if (tid() == 0) {
+        cplx<T> al = Vp[jj * nb + jj];
+        double aa = sqrt(static_cast<double>(cabs2(al)));
+        double nx = sqrt(nx2);
+        double pr = aa > 0 ? al.re / aa : 1.0, pi = aa > 0 ? al.im / aa : 0.0;
+        dm[0] = -pr * nx;  // gamma
+        dm[1] = -pi * nx;
+        dm[2] = 1.0 / sqrt(2.0 * nx * (nx + aa));  // 1 / ||x - gamma e_1||
+      }
+      __syncthreads();
+      const cplx<T> gam = cmake<T>(static_cast<T>(dm[0]), static_cast<T>(dm[1]));
+      const T sc = static_cast<T>(dm[2]);
+      for (int i = tid(); i < mr; i += kThreads) {
+        cplx<T> u = cmake<T>(0, 0);
+        if (i >= jj) {
+          cplx<T> x = Vp[i * nb + jj];
+          if (i == jj) x = cmake<T>(x.re - gam.re, x.im - gam.im);
+          u = cscale(x, sc);
+          B[static_cast<int64_t>(j0 + i) * ld + j0 + jj] = i == jj ? gam : cmake<T>(0, 0);
+        }
+        Vp[i * nb + jj] = u;
+      }
+      __syncthreads();
+      // the rest of the panel: b <- b - 2 u (u^dag b), one warp per column
+      for (int c = jj + 1 + warp_id(); c < jb; c += kWarps) {
+        T sr = 0, si = 0;
+        for (int i = jj + lane_id(); i < mr; i += 32) {
+          const cplx<T> u = Vp[i * nb + jj], b = Vp[i * nb + c];
+          sr += u.re * b.re + u.im * b.im;
+          si += u.re * b.im - u.im * b.re;
+        }
+        sr = __shfl_sync(0xffffffffu, warp_sum(sr), 0);
+        si = __shfl_sync(0xffffffffu, warp_sum(si), 0);
+        const cplx<T> s2 = cmake<T>(T(2) * sr, T(2) * si);
+        for (int i = jj + lane_id(); i < mr; i += 32) {
+          const cplx<T> t = cmul(Vp[i * nb + jj], s2);
+          cplx<T> &b = Vp[i * nb + c];
+          b = cmake<T>(b.re - t.re, b.im - t.im);
+        }
+      }
+      __syncthreads();
+    }
+    if (j0 + jb >= n) continue;  // no trailing columns
+    // G (strictly upper part), then T by its column recursion
+    for (int pr = warp_id(); pr < jb * jb; pr += kWarps) {
+      const int a = pr / jb, b = pr % jb;
+      if (a >= b) continue;
+      T gr = 0, gi = 0;
+      for (int i = b + lane_id(); i < mr; i += 32) {  // u_b vanishes above row b
+        const cplx<T> x = Vp[i * nb + a], y = Vp[i * nb + b];
+        gr += x.re * y.re + x.im * y.im;
+        gi += x.re * y.im - x.im * y.re;
+      }
+      gr = warp_sum(gr);
+      gi = warp_sum(gi);
+      if (lane_id() == 0) G[a * nb + b] = cmake<T>(gr, gi);
+    }
+    __syncthreads();
     if (tid() == 0) {
-      cplx<T> al = B[static_cast<int64_t>(j) * ld + j];
-      double aa = sqrt(static_cast<double>(cabs2(al)));
-      double nx = sqrt(nx2);
-      double pr = aa > 0 ? al.re / aa : 1.0, pi = aa > 0 ? al.im / aa : 0.0;
-      dm[0] = -pr * nx;  // gamma
-      dm[1] = -pi * nx;
-      dm[2] = 1.0 / sqrt(2.0 * nx * (nx + aa));  // 1 / ||x - gamma e_1||
-    }
-    __syncthreads();
-    const cplx<T> gam = cmake<T>(static_cast<T>(dm[0]), static_cast<T>(dm[1]));
-    const T sc = static_cast<T>(dm[2]);
-    for (int i = j + tid(); i < m; i += kThreads) {
-      cplx<T> x = B[static_cast<int64_t>(i) * ld + j];
-      if (i == j) x = cmake<T>(x.re - gam.re, x.im - gam.im);
-      uv[i - j] = cscale(x, sc);
-    }
-    __syncthreads();
-    // trailing columns: B[:, c] -= 2 u (u^dag B[:, c]), one thread per column
-    for (int c = j + 1 + tid(); c < n; c += kThreads) {
-      cplx<T> sdot = cmake<T>(0, 0);
-      for (int i = j; i < m; ++i) cfma(sdot, cconj(uv[i - j]), B[static_cast<int64_t>(i) * ld + c]);
-      sdot = cscale(sdot, T(2));
-      for (int i = j; i < m; ++i) {
-        cplx<T> &b = B[static_cast<int64_t>(i) * ld + c];
-        cplx<T> t = cmul(uv[i - j], sdot);
-        b = cmake<T>(b.re - t.re, b.im - t.im);
+      for (int k = 0; k < jb; ++k) {
+        Tm[k * nb + k] = cmake<T>(2, 0);
+        for (int a = 0; a < k; ++a) {
+          cplx<T> acc = cmake<T>(0, 0);
+          for (int b = a; b < k; ++b) cfma(acc, Tm[a * nb + b], G[b * nb + k]);
+          Tm[a * nb + k] = cscale(acc, T(-2));
+        }
       }
     }
-    for (int i = j + tid(); i < m; i += kThreads)
-      B[static_cast<int64_t>(i) * ld + j] = i == j ? gam : cmake<T>(0, 0);
+    __syncthreads();
+    // trailing columns: b <- b - V (T^dag (V^dag b))
+    for (int c = j0 + jb + tid(); c < n; c += kThreads) {
+      cplx<T> w[kQrPanel];
+#pragma unroll
+      for (int k = 0; k < kQrPanel; ++k) w[k] = cmake<T>(0, 0);
+      for (int i = 0; i < mr; ++i) {
+        const cplx<T> b = B[static_cast<int64_t>(j0 + i) * ld + c];
+#pragma unroll
+        for (int k = 0; k < kQrPanel; ++k)
+          if (k < jb) cfma(w[k], cconj(Vp[i * nb + k]), b);
+      }
+      // w <- T^dag w in place, highest index first: w'[a] = sum_{b<=a} conj(T[b][a]) w[b]
+#pragma unroll
+      for (int a = kQrPanel - 1; a >= 0; --a) {
+        if (a >= jb) continue;
+        cplx<T> acc = cmake<T>(0, 0);
+#pragma unroll
+        for (int b = 0; b <= a; ++b) cfma(acc, cconj(Tm[b * nb + a]), w[b]);
+        w[a] = acc;
+      }
+      for (int i = 0; i < mr; ++i) {
+        cplx<T> &bref = B[static_cast<int64_t>(j0 + i) * ld + c];
+        cplx<T> acc = bref;
+#pragma unroll
+        for (int k = 0; k < kQrPanel; ++k)
+          if (k < jb) {
+            const cplx<T> t = cmul(Vp[i * nb + k], w[k]);
+            acc = cmake<T>(acc.re - t.re, acc.im - t.im);
+          }
+        bref = acc;
+      }
+    }
     __syncthreads();
   }
 }
 
 // One-sided (Hestenes) Jacobi SVD.  Columns of C (m x n, column-major,
 // leading dimension m) are rotated pairwise until mutually orthogonal, so
-// that C V = U diag(sigma); V (column-major) accumulates the rotations.
+// that C V = U diag(sigma); V (column-major) accumulates the rotations unless
+// it is null (then only the rotated columns, U diag(sigma), are wanted).
 // Round-robin ordering, one warp per column pair, the pairs of a round are
 // disjoint.  A pair is left alone when its columns are orthogonal to the
 // rounding level of their dot products, or when one column is negligible
@@ -333,6 +438,10 @@ __device__ void onesided_sweep(int m, int n, cplx<T> *C, cplx<T> *V, int ldv, T 
         cp[i] = cmake<T>(cs * x.re - sn * y.re, cs * x.im - sn * y.im);
         cq[i] = cmake<T>(sn * x.re + cs * y.re, sn * x.im + cs * y.im);
       }
+      if (V == nullptr) {
+        if (lane_id() == 0) *flag = 1;
+        continue;
+      }
       cplx<T> *vp = V + static_cast<int64_t>(p) * ldv, *vq = V + static_cast<int64_t>(q) * ldv;
       for (int i = lane_id(); i < n; i += 32) {
         cplx<T> x = vp[i], y = cmul(uc, vq[i]);
@@ -352,7 +461,7 @@ __device__ __forceinline__ T onesided_tol(int m) {
 
 template <typename T>
 __device__ T onesided_prologue(int m, int n, const cplx<T> *C, cplx<T> *V, double *red) {
-  for (int e = tid(); e < n * n; e += kThreads) {
+  for (int e = tid(); V != nullptr && e < n * n; e += kThreads) {
     int j = e / n, i = e % n;
     V[e] = cmake<T>(i == j ? T(1) : T(0), 0);
   }
@@ -393,79 +502,188 @@ __device__ void svd_onesided(int m, int n, cplx<T> *C, cplx<T> *V, T *sig2, int 
   onesided_epilogue<T>(m, n, C, sig2);
 }
 
-// Blocked, for problems larger than shared memory: C and V in global memory;
-// the columns are split into blocks of bw, and every pair of blocks is
-// loaded into shared memory (sbuf), swept once there while a small unitary Q
-// (w x w) accumulates its rotations, written back, and applied to the
-// matching columns of V (V <- V Q, one thread per row).  Outer sweeps over
-// all block pairs repeat until no block pair rotates.
+// Blocked, for problems larger than shared memory: C (m x n, column-major)
+// and V (n x n, or null) stay in global memory and the columns are split into
+// blocks of bw.  One outer sweep first orthogonalises the columns inside every
+// block, then lets every pair of blocks exchange its cross pairs: the block
+// pairs of a tournament round are disjoint, and inside a block pair (I, J)
+// step t rotates the disjoint column pairs (b, (b + t) mod w_a) over the
+// smaller block's columns b and the larger block's columns, so each cross
+// pair is visited once per sweep.  A visited block (or block pair) is staged
+// in shared memory with its squared column norms, which the warp that rotates
+// a pair recomputes from the rotated columns, so testing a pair costs one dot
+// product.  With V, a w x w unitary Q accumulates the rotations of the visit
+// and is applied to V's matching columns afterwards, a chunk of V's rows at a
+// time through shared memory.  Outer sweeps repeat until one rotates nothing.
+template <typename T>
+__device__ void jacobi_rotate_staged(int m, int w, cplx<T> *Cb, cplx<T> *Q, T *nr, int p, int q, T tol,
+                                     T negligible, int *flag) {
+  const T al = nr[p], be = nr[q];
+  if (!(al > negligible) || !(be > negligible)) return;
+  cplx<T> *cp = Cb + static_cast<int64_t>(p) * m, *cq = Cb + static_cast<int64_t>(q) * m;
+  T gr = 0, gi = 0;
+  for (int i = lane_id(); i < m; i += 32) {
+    cplx<T> x = cp[i], y = cq[i];
+    gr += x.re * y.re + x.im * y.im;  // conj(x) y
+    gi += x.re * y.im - x.im * y.re;
+  }
+  gr = __shfl_sync(0xffffffffu, warp_sum(gr), 0);
+  gi = __shfl_sync(0xffffffffu, warp_sum(gi), 0);
+  const T absg = sqrt(gr * gr + gi * gi);
+  if (!(absg > tol * sqrt(al) * sqrt(be))) return;
+  const T zeta = (be - al) / (T(2) * absg);
+  const T az = fabs(zeta);
+  T t = az > T(1e10) ? T(0.5) / az : T(1) / (az + sqrt(T(1) + zeta * zeta));
+  if (zeta < 0) t = -t;
+  const T cs = T(1) / sqrt(T(1) + t * t), sn = t * cs;
+  const cplx<T> uc = cmake<T>(gr / absg, -gi / absg);  // conj(gamma / |gamma|)
+  T np = 0, nq = 0;
+  for (int i = lane_id(); i < m; i += 32) {
+    cplx<T> x = cp[i], y = cmul(uc, cq[i]);
+    cplx<T> xn = cmake<T>(cs * x.re - sn * y.re, cs * x.im - sn * y.im);
+    cplx<T> yn = cmake<T>(sn * x.re + cs * y.re, sn * x.im + cs * y.im);
+    cp[i] = xn;
+    cq[i] = yn;
+    np += cabs2(xn);
+    nq += cabs2(yn);
+  }
+  np = __shfl_sync(0xffffffffu, warp_sum(np), 0);
+  nq = __shfl_sync(0xffffffffu, warp_sum(nq), 0);
+  if (Q != nullptr) {
+    cplx<T> *qp = Q + static_cast<int64_t>(p) * w, *qq = Q + static_cast<int64_t>(q) * w;
+    for (int i = lane_id(); i < w; i += 32) {
+      cplx<T> x = qp[i], y = cmul(uc, qq[i]);
+      qp[i] = cmake<T>(cs * x.re - sn * y.re, cs * x.im - sn * y.im);
+      qq[i] = cmake<T>(sn * x.re + cs * y.re, sn * x.im + cs * y.im);
+    }
+  }
+  __syncwarp();
+  if (lane_id() == 0) {
+    nr[p] = np;
+    nr[q] = nq;
+    *flag = 1;
+  }
+}
+
 template <typename T>
 __device__ void svd_onesided_blocked(int m, int n, cplx<T> *C, cplx<T> *V, T *sig2, int *flag,
                                      double *red, cplx<T> *sbuf, int sbuf_elems) {
   const T negligible = onesided_prologue<T>(m, n, C, V, red);
   const T tol = onesided_tol<T>(m);
+  // staged block pair: Q (w x w, only with V), norms (w complex slots),
+  // columns (m x w)
+  const bool withV = V != nullptr;
   int bw = 32;
-  while (bw > 1 && static_cast<int64_t>(m) * 2 * bw + 4 * bw * bw > sbuf_elems) --bw;
+  while (bw > 1 && static_cast<int64_t>(m) * 2 * bw + (withV ? 4 * bw * bw : 0) + 2 * bw > sbuf_elems) --bw;
+  if (bw > kWarps) bw -= bw % kWarps;  // whole waves of warps per step
   const int nb = (n + bw - 1) / bw, nbe = nb + (nb & 1);
   const int max_sweeps = sizeof(T) == 4 ? kMaxBlockedSweepsF : kMaxBlockedSweepsD;
-  cplx<T> *Cb = sbuf;
   int *any = flag + 1;
+
+  auto visit = [&](int I, int J) {
+    const bool self = I == J;
+    const int c0 = I * bw, wI = min(bw, n - c0);
+    const int c1 = J * bw, wJ = self ? 0 : min(bw, n - c1);
+    const int w = wI + wJ;
+    auto gcol = [&](int c) { return c < wI ? c0 + c : c1 + (c - wI); };
+    const int qe = withV ? w * w : 0;
+    cplx<T> *Q = withV ? sbuf : nullptr;
+    T *nr = reinterpret_cast<T *>(sbuf + qe);
+    cplx<T> *Cb = sbuf + qe + w;
+    for (int e = tid(); e < m * w; e += kThreads) {
+      const int c = e / m, i = e % m;
+      Cb[e] = C[static_cast<int64_t>(gcol(c)) * m + i];
+    }
+    for (int e = tid(); e < qe; e += kThreads) Q[e] = cmake<T>((e / w) == (e % w) ? T(1) : T(0), 0);
+    __syncthreads();
+    for (int c = warp_id(); c < w; c += kWarps) {
+      T a = 0;
+      for (int i = lane_id(); i < m; i += 32) a += cabs2(Cb[static_cast<int64_t>(c) * m + i]);
+      a = __shfl_sync(0xffffffffu, warp_sum(a), 0);
+      if (lane_id() == 0) nr[c] = a;
+    }
+    if (tid() == 0) *flag = 0;
+    __syncthreads();
+    if (self) {
+      const int mm = w + (w & 1), half = mm / 2;
+      for (int round = 0; round < mm - 1; ++round) {
+        for (int pi = warp_id(); pi < half; pi += kWarps) {
+          int p, q;
+          if (pi == 0) { p = mm - 1; q = round; }
+          else { p = (round + pi) % (mm - 1); q = (round - pi + (mm - 1)) % (mm - 1); }
+          if (p > q) { int tt = p; p = q; q = tt; }
+          if (q >= w) continue;
+          jacobi_rotate_staged<T>(m, w, Cb, Q, nr, p, q, tol, negligible, flag);
+        }
+        __syncthreads();
+      }
+    } else {
+      const bool i_larger = wI >= wJ;
+      const int wa = i_larger ? wI : wJ, wb = i_larger ? wJ : wI;
+      for (int t = 0; t < wa; ++t) {
+        for (int b = warp_id(); b < wb; b += kWarps) {
+          const int a = (b + t) % wa;
+          const int p = i_larger ? a : b, q = wI + (i_larger ? b : a);
+          jacobi_rotate_staged<T>(m, w, Cb, Q, nr, p, q, tol, negligible, flag);
+        }
+        __syncthreads();
+      }
+    }
+    const int rotated = *flag;
+    __syncthreads();
+    if (!rotated) return;
+    for (int e = tid(); e < m * w; e += kThreads) {
+      const int c = e / m, i = e % m;
+      C[static_cast<int64_t>(gcol(c)) * m + i] = Cb[e];
+    }
+    __syncthreads();
+    // V[:, cols] <- V[:, cols] Q, rows staged in the column buffer
+    const int rows_cap = (sbuf_elems - qe - w) / w;
+    for (int i0 = 0; withV && i0 < n; i0 += rows_cap) {
+      const int rows = min(rows_cap, n - i0);
+      for (int e = tid(); e < rows * w; e += kThreads) {
+        const int c = e / rows, i = e % rows;
+        Cb[e] = V[static_cast<int64_t>(gcol(c)) * n + i0 + i];
+      }
+      __syncthreads();
+      // four output columns per thread: one staged element feeds four FMAs
+      const int groups = (w + 3) / 4;
+      for (int e = tid(); e < rows * groups; e += kThreads) {
+        const int g = e / rows, i = e % rows, cb = 4 * g;
+        cplx<T> acc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = cmake<T>(0, 0);
+        for (int j = 0; j < w; ++j) {
+          const cplx<T> v = Cb[j * rows + i];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (cb + u < w) cfma(acc[u], v, Q[(cb + u) * w + j]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (cb + u < w) V[static_cast<int64_t>(gcol(cb + u)) * n + i0 + i] = acc[u];
+      }
+      __syncthreads();
+    }
+    if (tid() == 0) *any = 1;
+  };
+
   for (int sweep = 0; sweep < max_sweeps && n > 1; ++sweep) {
     if (tid() == 0) *any = 0;
     __syncthreads();
+    for (int I = 0; I < nb; ++I) visit(I, I);
     for (int round = 0; round < nbe - 1; ++round) {
       for (int bp = 0; bp < nbe / 2; ++bp) {
         int I, J;
         if (bp == 0) { I = nbe - 1; J = round; }
         else { I = (round + bp) % (nbe - 1); J = (round - bp + (nbe - 1)) % (nbe - 1); }
-        if (I > J) { int t = I; I = J; J = t; }
+        if (I > J) { int tt = I; I = J; J = tt; }
         if (J >= nb) continue;
-        const int c0 = I * bw, wI = min(bw, n - c0), c1 = J * bw, wJ = min(bw, n - c1);
-        const int w = wI + wJ;
-        cplx<T> *Q = Cb + static_cast<int64_t>(m) * w;
-        for (int e = tid(); e < m * w; e += kThreads) {
-          int c = e / m, i = e % m;
-          int gc = c < wI ? c0 + c : c1 + (c - wI);
-          Cb[e] = C[static_cast<int64_t>(gc) * m + i];
-        }
-        for (int e = tid(); e < w * w; e += kThreads) Q[e] = cmake<T>((e / w) == (e % w) ? T(1) : T(0), 0);
-        // up to three sweeps inside the block pair: one alone converges too
-        // slowly over the outer sweeps
-        int rotated = 0;
-        for (int inner = 0; inner < 3; ++inner) {
-          if (tid() == 0) *flag = 0;
-          __syncthreads();
-          onesided_sweep<T>(m, w, Cb, Q, w, tol, negligible, flag);
-          const int f = *flag;
-          __syncthreads();
-          if (!f) break;
-          rotated = 1;
-        }
-        if (!rotated) continue;
-        for (int e = tid(); e < m * w; e += kThreads) {
-          int c = e / m, i = e % m;
-          int gc = c < wI ? c0 + c : c1 + (c - wI);
-          C[static_cast<int64_t>(gc) * m + i] = Cb[e];
-        }
-        for (int i = tid(); i < n; i += kThreads) {
-          cplx<T> row[64];
-#pragma unroll 4
-          for (int c = 0; c < w; ++c) {
-            int gc = c < wI ? c0 + c : c1 + (c - wI);
-            row[c] = V[static_cast<int64_t>(gc) * n + i];
-          }
-          for (int c = 0; c < w; ++c) {
-            cplx<T> acc = cmake<T>(0, 0);
-            for (int j = 0; j < w; ++j) cfma(acc, row[j], Q[static_cast<int64_t>(c) * w + j]);
-            int gc = c < wI ? c0 + c : c1 + (c - wI);
-            V[static_cast<int64_t>(gc) * n + i] = acc;
-          }
-        }
-        if (tid() == 0) *any = 1;
-        __syncthreads();
+        visit(I, J);
       }
     }
-    int f = *any;
+    __syncthreads();
+    const int f = *any;
     __syncthreads();
     if (!f) break;
   }
@@ -813,7 +1031,7 @@ __device__ double mps_prepare(const EngineParams &P, const Smem<T> &S, int64_t s
       __syncthreads();
       return 0.0;
     }
-    qr_r_inplace<T>(m, Dr, X.t, Dr, S.uvec, S.red, S.dmisc + 4);
+    qr_r_inplace<T>(m, Dr, X.t, Dr, S.jbuf, P.svd_elems, S.red, S.dmisc + 4);
     if (tid() == 0) S.dmisc[D_FLOPS] += qr_flops(m, Dr);
     const int rn = min(m, Dr);
     cplx<T> *Rout = X.g + S.goff[k + 1 - a];
@@ -872,7 +1090,7 @@ __device__ void mps_finish(const EngineParams &P, const Smem<T> &S, int64_t shot
     // is decomposed in double precision: FP32 Jacobi rotations leave the small
     // singular directions with an absolute error of about sqrt(#rotations)
     // eps sigma_1, which would be dropped or kept wrongly at every sweep.
-    bool svd64 = false;
+    bool svd64 = false, vec_from_columns = false;
     if constexpr (sizeof(T) == 4) svd64 = 2 * (r * n2 + n2 * n2) <= P.svd_elems;
     if (svd64) {
       cplx<double> *Cd = reinterpret_cast<cplx<double> *>(S.jbuf), *Vd = Cd + r * n2;
@@ -889,14 +1107,38 @@ __device__ void mps_finish(const EngineParams &P, const Smem<T> &S, int64_t shot
       for (int i = tid(); i < n2; i += kThreads) X.lam[i] = static_cast<T>(sd[i]);
       __syncthreads();
       Vc = X.v;
-    } else {
+    } else if (in_smem) {
       for (int e = tid(); e < r * n2; e += kThreads) {
         int i = e / n2, j = e % n2;
         Cc[j * r + i] = X.y[e];
       }
       __syncthreads();
-      if (in_smem) svd_onesided<T>(r, n2, Cc, Vc, X.lam, &S.misc[M_JFLAG], S.red);
-      else svd_onesided_blocked<T>(r, n2, Cc, Vc, X.lam, &S.misc[M_JFLAG], S.red, S.jbuf, P.svd_elems);
+      svd_onesided<T>(r, n2, Cc, Vc, X.lam, &S.misc[M_JFLAG], S.red);
+    } else {
+      // Large bond: C = Q1 R1 (Householder), then one-sided Jacobi on
+      // X = R1^dag (n2 x kx), whose columns converge in a few sweeps because
+      // R1 is already nearly diagonal.  X V_x = U_x Sigma gives
+      // R1 = V_x Sigma U_x^dag, so the right singular vectors of C are the
+      // normalised columns of the rotated X and no rotation is accumulated.
+      // Rows of R1 (row-major, ld n2) are the conjugated columns of X
+      // (column-major, ld n2) in place.
+      if (r > kMaxVec) {
+        if (tid() == 0) S.misc[M_FAIL] = STN_EOVERFLOW;
+        __syncthreads();
+        return;
+      }
+      qr_r_inplace<T>(r, n2, X.y, n2, S.jbuf, P.svd_elems, S.red, S.dmisc + 4);
+      const int kx = min(r, n2);
+      const bool x_smem = n2 * kx <= P.svd_elems;
+      cplx<T> *Xc = x_smem ? S.jbuf : X.y;
+      for (int e = tid(); e < n2 * kx; e += kThreads) Xc[e] = cconj(X.y[e]);
+      __syncthreads();
+      if (x_smem) svd_onesided<T>(n2, kx, Xc, nullptr, X.lam, &S.misc[M_JFLAG], S.red);
+      else svd_onesided_blocked<T>(n2, kx, Xc, nullptr, X.lam, &S.misc[M_JFLAG], S.red, S.jbuf, P.svd_elems);
+      for (int i = kx + tid(); i < n2; i += kThreads) X.lam[i] = T(0);
+      __syncthreads();
+      Vc = Xc;
+      vec_from_columns = true;
     }
     if (tid() == 0) S.dmisc[D_FLOPS] += gemm_flops(r, n2, Dl) + svd_flops(r, n2);
     for (int i = tid(); i < n2; i += kThreads) {
@@ -926,9 +1168,15 @@ __device__ void mps_finish(const EngineParams &P, const Smem<T> &S, int64_t shot
     __syncthreads();
     const int keep = S.misc[M_KEEP];
     // sorted, kept right singular vectors: Vs[:, c] = V[:, perm[c]], c < keep
+    // (or the rotated column of X over its norm)
     for (int e = tid(); e < n2 * keep; e += kThreads) {
       int i = e / keep, c = e % keep;
-      X.vs[i * keep + c] = Vc[static_cast<int64_t>(S.perm[c]) * n2 + i];
+      cplx<T> v = Vc[static_cast<int64_t>(S.perm[c]) * n2 + i];
+      if (vec_from_columns) {
+        T l = S.lam[c];
+        v = l > T(0) ? cscale(v, T(1) / sqrt(l)) : cmake<T>(i == c ? T(1) : T(0), 0);
+      }
+      X.vs[i * keep + c] = v;
     }
     __syncthreads();
     reorthonormalize<T>(n2, keep, X.vs, X.e, X.y, S.tile);
@@ -1448,7 +1696,24 @@ __global__ void __launch_bounds__(kThreads, 1) dense_check_kernel(int what, int 
   cplx<T> *uv = reinterpret_cast<cplx<T> *>(flag + 16);
   cplx<T> *buf = uv + kMaxVec;
   if (what == 0) {
-    qr_r_inplace<T>(m, n, A, n, uv, red, dm);
+    qr_r_inplace<T>(m, n, A, n, buf, SvdSmem<T>::elems, red, dm);
+  } else if (use_smem == 3) {
+    // the large-bond path of the truncation sweep: A row-major (m x n),
+    // R factor, Jacobi on X = R^dag (n x k), V = normalised columns of X
+    qr_r_inplace<T>(m, n, A, n, buf, SvdSmem<T>::elems, red, dm);
+    const int k = min(m, n);
+    const bool x_smem = n * k <= SvdSmem<T>::elems;
+    cplx<T> *Xc = x_smem ? buf : A;
+    for (int e = tid(); e < n * k; e += kThreads) Xc[e] = cconj(A[e]);
+    __syncthreads();
+    if (x_smem) svd_onesided<T>(n, k, Xc, nullptr, sig2, flag, red);
+    else svd_onesided_blocked<T>(n, k, Xc, nullptr, sig2, flag, red, buf, SvdSmem<T>::elems);
+    for (int e = tid(); e < n * n; e += kThreads) {
+      const int c = e / n;
+      const T l = c < k ? sig2[c] : T(0);
+      V[e] = l > T(0) ? cscale(Xc[e], T(1) / sqrt(l)) : cmake<T>(0, 0);
+    }
+    for (int c = k + tid(); c < n; c += kThreads) sig2[c] = T(0);
   } else {
     cplx<T> *C = A, *VV = V;
     if (use_smem == 1) {
@@ -1470,7 +1735,7 @@ template <typename T>
 static cudaError_t launch_dense_check_t(int what, int m, int n, void *A, void *V, void *sig2, int use_smem,
                                         cudaStream_t s) {
   size_t smem = sizeof(double) * (kThreads + 16) + sizeof(int) * 16 + sizeof(cplx<T>) * kMaxVec;
-  if (use_smem) smem += sizeof(cplx<T>) * SvdSmem<T>::elems;  // 1: matrix in smem, 2: blocked
+  smem += sizeof(cplx<T>) * SvdSmem<T>::elems;  // QR panel, SVD matrix or staged column blocks
   cudaError_t e = cudaFuncSetAttribute(dense_check_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;

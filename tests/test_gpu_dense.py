@@ -32,7 +32,8 @@ def rand(rng, m, n, decay=0.0):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("m,n", [(2, 1), (8, 4), (64, 32), (33, 47), (96, 48), (300, 120)])
+@pytest.mark.parametrize("m,n", [(2, 1), (8, 4), (64, 32), (33, 47), (96, 48), (300, 120), (1024, 512),
+                                 (40, 300)])
 def test_qr_r_factor(precision, m, n):
     rng = np.random.default_rng(m * 1000 + n)
     a = rand(rng, m, n, decay=0.05)
@@ -78,3 +79,36 @@ def test_onesided_svd(precision, m, n, smem, decay):
     gram = us.conj().T @ us
     off = gram - np.diag(np.diag(gram))
     assert np.abs(off).max() < TOL[precision] * 10 * s_ref[0] ** 2
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("m,n,decay", [(40, 24, 0.3), (64, 128, 0.1), (200, 150, 0.05), (256, 512, 0.05),
+                                       (512, 512, 0.03)])
+def test_large_bond_svd(precision, m, n, decay):
+    """The large-bond path of the truncation sweep (Householder R factor,
+    then one-sided Jacobi on R^dag): singular values, and the truncation of
+    A to its leading right singular vectors, on graded MPS-like spectra."""
+    rng = np.random.default_rng(11 * m + n)
+    a = rand(rng, m, n, decay=decay)
+    dc = torch.tensor(a, dtype=CDT[precision], device="cuda")  # row-major
+    dv = torch.zeros((n, n), dtype=CDT[precision], device="cuda")
+    ds = torch.zeros(n, dtype=RDT[precision], device="cuda")
+    stn.dense_svd(precision, m, n, dc.data_ptr(), dv.data_ptr(), ds.data_ptr(), 3)
+    torch.cuda.synchronize()
+    v = dv.cpu().numpy().T.astype(np.complex128)  # columns = right vectors
+    sig2 = ds.cpu().numpy().astype(np.float64)
+    k = min(m, n)
+    assert np.all(sig2[k:] == 0)
+    u_ref, s_ref, vh_ref = np.linalg.svd(a, full_matrices=False)
+    order = np.argsort(-sig2)
+    got = np.sqrt(np.maximum(sig2[order], 0))[:k]
+    assert np.abs(got - s_ref).max() < TOL[precision] * 10 * s_ref[0]
+    # the kept right vectors: orthonormal where sigma is well above rounding,
+    # and A projected on the leading `keep` of them is the optimal truncation
+    keep = max(1, int(np.sum(s_ref > 1e-3 * s_ref[0])))
+    vk = v[:, order[:keep]]
+    assert np.abs(vk.conj().T @ vk - np.eye(keep)).max() < TOL[precision] * 1e3
+    best = (u_ref[:, :keep] * s_ref[:keep]) @ vh_ref[:keep]
+    q, _ = np.linalg.qr(vk)  # the sweep re-orthonormalises the kept vectors
+    err = np.abs(a @ q @ q.conj().T - best).max()
+    assert err < TOL[precision] * 10 * s_ref[0], err
