@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", default="stn", choices=["stn", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chi-cap", type=int, default=None,
+                    help="override the bond cap (smaller profiling captures only; not a bench line)")
     return ap.parse_args()
 
 
@@ -175,6 +177,8 @@ def reference_arm(args, w):
 def main():
     args = parse()
     w = D5_BENCH
+    if args.chi_cap is not None and args.chi_cap != w.chi_cap:
+        w = w.with_(chi_cap=args.chi_cap, name=f"{w.name}_cap{args.chi_cap}")
     if args.impl == "reference":
         reference_arm(args, w)
         return
@@ -213,7 +217,9 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    seg_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(segs + 1)] for _ in range(K // segs)]
     flops0 = sim.algorithmic_flops()
+    prof0 = sim.profile_counters()
     launches = 0
     # timed: K segments = K / 6 complete batches.  The host clock also covers the
     # angle upload from pinned memory and each batch's record download (e2e).
@@ -224,15 +230,29 @@ def main():
         sim.begin_batch(B, base + (W + b) * B)
         launches += 1
         for seg in range(segs):
+            seg_ev[b][seg].record(stream)
             sim.apply_round_device(seg, d_theta.data_ptr())
             launches += 1
+        seg_ev[b][segs].record(stream)
         if b + 1 == K // segs:
             ev1.record(stream)
         sim.read_records_into(rec_host.data_ptr())
     host_s = time.perf_counter() - t_host
     torch.cuda.synchronize()
     flops = sim.algorithmic_flops() - flops0
+    prof1 = sim.profile_counters()
     clk = clocks.stop()
+    seg_ms = [statistics.mean(seg_ev[b][g].elapsed_time(seg_ev[b][g + 1]) for b in range(K // segs))
+              for g in range(segs)]
+    dprof = {k: prof1[k] - prof0[k] for k in prof1}
+    loop = max(dprof["op_loop_cycles"], 1.0)
+    phases = {"segment_ms": [round(x, 3) for x in seg_ms],
+              "cycle_share": {k.replace("_cycles", ""): round(dprof[k] / loop, 4)
+                              for k in ("left_sweep_cycles", "svd_cycles", "right_sweep_rest_cycles",
+                                        "expectation_cycles")},
+              "svds_per_shot": {"shared_memory": dprof["svd_count_shared"] / (B * (K // segs)),
+                                "large_bond": dprof["svd_count_large"] / (B * (K // segs))},
+              "source": "stn_profile_counters: SM clock cycles of each CTA per phase, over the timed batches"}
     secs = ev0.elapsed_time(ev1) / 1000.0
     if pg:
         t = torch.tensor([secs, host_s], dtype=torch.float64, device="cuda")
@@ -272,7 +292,7 @@ def main():
                            "l2": "per-shot MPS state (GBs) larger than L2; no flush",
                            "parallelism": f"shots sharded over {ws} rank(s)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk}
+                "clocks": clk, "phases": phases}
         print(json.dumps(line), flush=True)
     sim.close()
     if pg:

@@ -147,6 +147,16 @@ const uint8_t *stn_device_records(const stn_ctx *ctx);
  * instruction mix.  Used to place measured throughput on a roofline. */
 stn_status stn_algorithmic_flops(stn_ctx *ctx, double *h_total);
 
+/* Phase counters of all round launches since creation, summed over shot
+ * slots (synchronises).  h_out[8]: SM clock cycles spent by the CTAs in
+ * [0] the left (R-factor) sweep, [1] the right sweep's SVDs, [2] the rest of
+ * the right sweep (contractions, sorting, new sites), [3] expectation values,
+ * [4] the whole op loop (so [4] - [0..3] is the tableau and bookkeeping);
+ * then counts of [5] shared-memory SVDs and [6] large-bond SVDs (Householder
+ * R factor plus Jacobi on R^dag); [7] is zero.  Diagnostics only: they
+ * explain where a round's time goes, they are not part of the path. */
+stn_status stn_profile_counters(stn_ctx *ctx, double *h_out);
+
 /* Inverse tableau of one shot of the current batch (synchronises): rows
  * X_0..X_{n-1}, Z_0..Z_{n-1}; row r is i^phase[r] X^x Z^z with x bits in
  * h_x[r*W .. r*W+W-1] (W = ceil(n/64) words, qubit q at bit q%64 of word

@@ -37,6 +37,7 @@ struct stn_ctx {
   int *d_chi = nullptr, *d_center = nullptr, *d_maxchi = nullptr, *d_near = nullptr,
       *d_status = nullptr;
   double *d_logp = nullptr, *d_disc = nullptr, *d_born = nullptr, *d_flops = nullptr;
+  double *d_prof = nullptr;
   uint8_t *d_rec = nullptr;
   void *d_scratch = nullptr;
   int *d_err = nullptr;
@@ -103,6 +104,7 @@ stn::EngineParams params(const stn_ctx *c, int seg, const double *d_theta) {
   p.records = c->d_rec;
   p.born = c->d_born;
   p.flops = c->d_flops;
+  p.prof = c->d_prof;
   p.scratch = c->d_scratch;
   p.scratch_elems = c->plan.total;
   p.ap_elems = c->plan.ap_elems;
@@ -205,6 +207,7 @@ stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_strea
   A(dalloc(c, &c->d_disc, sizeof(double) * S));
   A(dalloc(c, &c->d_born, sizeof(double) * S * c->prog.n_meas));
   A(dalloc(c, &c->d_flops, sizeof(double) * S));
+  A(dalloc(c, &c->d_prof, sizeof(double) * S * stn::kProfSlots));
   A(dalloc(c, &c->d_rec, static_cast<size_t>(S) * c->rec_bytes));
   A(dalloc(c, &c->d_scratch, c->elem * static_cast<size_t>(c->grid) * c->plan.total));
   A(dalloc(c, &c->d_err, sizeof(int)));
@@ -223,6 +226,7 @@ stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_strea
                         cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_flops, 0, sizeof(double) * S, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_prof, 0, sizeof(double) * S * stn::kProfSlots, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     stn_destroy(c);
@@ -374,6 +378,18 @@ stn_status stn_algorithmic_flops(stn_ctx *c, double *h_total) {
   double t = 0;
   for (double v : f) t += v;
   *h_total = t;
+  return STN_OK;
+}
+
+stn_status stn_profile_counters(stn_ctx *c, double *h_out) {
+  if (!c || !h_out) return STN_EINVAL;
+  stn_status st = stn_sync(c);
+  if (st != STN_OK) return st;
+  std::vector<double> f(static_cast<size_t>(c->max_shots) * stn::kProfSlots);
+  cudaError_t e = cudaMemcpy(f.data(), c->d_prof, sizeof(double) * f.size(), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stn_profile_counters");
+  for (int i = 0; i < stn::kProfSlots; ++i) h_out[i] = 0;
+  for (size_t k = 0; k < f.size(); ++k) h_out[k % stn::kProfSlots] += f[k];
   return STN_OK;
 }
 

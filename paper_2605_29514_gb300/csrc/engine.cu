@@ -843,7 +843,17 @@ __device__ Smem<T> carve(char *base, int n, int W, int svd_elems) {
 // misc slots
 enum { M_LO = 0, M_HI, M_A, M_B, M_CENTER, M_FAIL, M_KEEP, M_MAXCHI, M_CASEB, M_J, M_BIT, M_LIDX, M_OUTCOME, M_JFLAG };
 // dmisc slots
-enum { D_DISC = 0, D_LOGP, D_E, D_NORM, D_FLOPS = 8 };
+enum { D_DISC = 0, D_LOGP, D_E, D_NORM, D_FLOPS = 8, D_PROF = 8 };  // D_PROF + 1 + ProfSlot
+
+// Adds the cycles since `t` to a phase slot and restarts `t` (thread 0 only;
+// callers sit just after a CTA barrier so the CTA is in step).
+__device__ __forceinline__ void prof_mark(double *dmisc, int slot, long long &t) {
+  if (threadIdx.x == 0) {
+    const long long now = clock64();
+    dmisc[D_PROF + 1 + slot] += static_cast<double>(now - t);
+    t = now;
+  }
+}
 
 // Per-CTA scratch partition (complex elements).
 template <typename T>
@@ -1073,6 +1083,7 @@ __device__ void mps_finish(const EngineParams &P, const Smem<T> &S, int64_t shot
   }
   auto Dbond = [&](int k) { return (k > sp.lo && k <= sp.hi) ? 2 * chi[k] : chi[k]; };
   const cplx<T> one = cmake<T>(1, 0), zero = cmake<T>(0, 0);
+  long long tp = clock64();
   // right sweep
   int kappa = Dbond(b + 1);
   const cplx<T> *M = X.ap + S.off[b - a];
@@ -1083,6 +1094,7 @@ __device__ void mps_finish(const EngineParams &P, const Smem<T> &S, int64_t shot
     const cplx<T> *Rk = X.g + S.goff[k - a];
     // C = R_k M (r x n2), then its SVD
     cgemm<T, 0, 0>(r, n2, Dl, one, Rk, Dl, M, n2, zero, X.y, n2, S.tile);
+    prof_mark(S.dmisc, PROF_RIGHT, tp);
     const bool in_smem = r * n2 + n2 * n2 <= P.svd_elems;
     cplx<T> *Cc = in_smem ? S.jbuf : X.h;
     cplx<T> *Vc = in_smem ? S.jbuf + r * n2 : X.v;
@@ -1140,7 +1152,12 @@ __device__ void mps_finish(const EngineParams &P, const Smem<T> &S, int64_t shot
       Vc = Xc;
       vec_from_columns = true;
     }
-    if (tid() == 0) S.dmisc[D_FLOPS] += gemm_flops(r, n2, Dl) + svd_flops(r, n2);
+    __syncthreads();
+    prof_mark(S.dmisc, PROF_SVD, tp);
+    if (tid() == 0) {
+      S.dmisc[D_FLOPS] += gemm_flops(r, n2, Dl) + svd_flops(r, n2);
+      S.dmisc[D_PROF + 1 + (vec_from_columns ? PROF_NSVD_LARGE : PROF_NSVD_SMALL)] += 1.0;
+    }
     for (int i = tid(); i < n2; i += kThreads) {
       if (!isfinite(static_cast<double>(X.lam[i]))) {
         S.misc[M_FAIL] = STN_ENUMERIC;
@@ -1200,6 +1217,7 @@ __device__ void mps_finish(const EngineParams &P, const Smem<T> &S, int64_t shot
     M = X.mbuf;
     kappa = keep;
   }
+  prof_mark(S.dmisc, PROF_RIGHT, tp);
   // centre site a = M (chi[a] x 2 x kappa), renormalised
   cplx<T> *Aa = site_ptr<T>(P, shot, a);
   const int64_t tot = static_cast<int64_t>(chi[a]) * 2 * kappa;
@@ -1216,13 +1234,6 @@ __device__ void mps_finish(const EngineParams &P, const Smem<T> &S, int64_t shot
     S.misc[M_MAXCHI] = mx;
   }
   __syncthreads();
-}
-
-template <typename T>
-__device__ void mps_apply_compress(const EngineParams &P, const Smem<T> &S, int64_t shot,
-                                   const Scratch<T> &X, int a, int b) {
-  mps_prepare<T>(P, S, shot, X, a, b);
-  mps_finish<T>(P, S, shot, X, a, b);
 }
 
 // <phi| i^m X^x Z^z |phi> over sites [a, b] (centre inside, so the rest of
@@ -1479,8 +1490,10 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
       S.dmisc[D_DISC] = P.disc[shot];
       S.dmisc[D_LOGP] = P.logp[shot];
       S.dmisc[D_FLOPS] = 0.0;
+      for (int i = 0; i < kProfSlots - 1; ++i) S.dmisc[D_PROF + 1 + i] = 0.0;
     }
     __syncthreads();
+    long long t_ops = clock64();
     const uint64_t gshot = P.shot_offset + static_cast<uint64_t>(shot);
     for (int oi = P.op_begin; oi < P.op_end; ++oi) {
       if (S.misc[M_FAIL]) break;
@@ -1580,6 +1593,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
               for (int k = a; k <= b + 1; ++k) mx = max(mx, S.chi[k]);
               exact64 = mx <= kExpect64Chi && need <= sizeof(cplx<T>) * static_cast<size_t>(P.svd_elems);
             }
+            long long tq = clock64();
             double e = 0.0;
             if constexpr (sizeof(T) == 4) {
               if (exact64) e = mps_expect64<T>(P, S, shot, a, b, mb & 3);
@@ -1590,7 +1604,9 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
             const int small = e >= 0.0 ? 1 : 0;
             if (tid() == 0) set_meas_spec<T>(S, small);
             __syncthreads();
+            prof_mark(S.dmisc, PROF_EXPECT, tq);
             double ps = fmin(1.0, fmax(0.0, mps_prepare<T>(P, S, shot, X, a, b)));
+            prof_mark(S.dmisc, PROF_LEFT, tq);
             // in double precision the expectation value is as accurate as the
             // projected norm; in single precision it is preferred only where
             // it was contracted in double
@@ -1612,10 +1628,17 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
             caseB = S.misc[M_CASEB];
             lidx = S.misc[M_LIDX];
             outcome = S.misc[M_OUTCOME];
+            tq = clock64();
             if (outcome != small) mps_prepare<T>(P, S, shot, X, a, b);
+            __syncthreads();
+            prof_mark(S.dmisc, PROF_LEFT, tq);
             mps_finish<T>(P, S, shot, X, a, b);
           } else {
-            mps_apply_compress<T>(P, S, shot, X, a, b);
+            long long tq = clock64();
+            mps_prepare<T>(P, S, shot, X, a, b);
+            __syncthreads();
+            prof_mark(S.dmisc, PROF_LEFT, tq);
+            mps_finish<T>(P, S, shot, X, a, b);
           }
           if (meas) {
             if (caseB) tableau_caseB(S.tx, S.tz, S.tm, n, W, S.ppx, S.ppz, S.misc[M_J], lidx);
@@ -1645,6 +1668,8 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
       P.disc[shot] = S.dmisc[D_DISC];
       P.logp[shot] = S.dmisc[D_LOGP];
       P.flops[shot] += S.dmisc[D_FLOPS];
+      S.dmisc[D_PROF + 1 + PROF_OPS] = static_cast<double>(clock64() - t_ops);
+      for (int i = 0; i < kProfSlots - 1; ++i) P.prof[shot * kProfSlots + i] += S.dmisc[D_PROF + 1 + i];
       if (S.misc[M_FAIL]) atomicCAS(P.err, 0, S.misc[M_FAIL]);
     }
     __syncthreads();

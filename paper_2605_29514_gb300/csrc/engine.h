@@ -10,6 +10,12 @@ namespace stn {
 
 constexpr int kThreads = 256;   // threads per CTA of the round kernel
 constexpr double kNearThreshold = 1e-5;
+// Phase counters (SM clock cycles of the CTA, summed over ops): left sweep,
+// right-sweep SVDs, the rest of the right sweep, expectation values, the whole
+// op loop; then counts of small (shared-memory) and large-bond SVDs.
+constexpr int kProfSlots = 8;
+enum ProfSlot { PROF_LEFT = 0, PROF_SVD, PROF_RIGHT, PROF_EXPECT, PROF_OPS, PROF_NSVD_SMALL,
+                PROF_NSVD_LARGE, PROF_SPARE };
 
 // Everything one segment launch needs.  Per-shot arrays are indexed by the
 // shot's position in the batch; per-CTA scratch by blockIdx.x.
@@ -38,6 +44,7 @@ struct EngineParams {
   uint8_t *records;         // [shot][rec_bytes]
   double *born;             // [shot][n_meas]
   double *flops;            // [shot] algorithmic FLOPs, cumulative over batches
+  double *prof;             // [shot][kProfSlots] SM cycles per phase, cumulative
   // per-CTA scratch, complex elements of the path's precision
   void *scratch;
   int64_t scratch_elems, ap_elems, g_elems;
