@@ -141,6 +141,25 @@ stn_status stn_read_records(stn_ctx *ctx, uint8_t *h_records, double *h_born,
  * ([shots][ceil(n_meas/8)] bytes, owned by the context). */
 const uint8_t *stn_device_records(const stn_ctx *ctx);
 
+/* Number of detectors of the program (Z-memory: the Z faces in round 0, every
+ * face from round 1 on, every Z face again at the final data readout). */
+int32_t stn_num_detectors(const stn_ctx *ctx);
+
+/* Detector bits and logical Z_L parity of the current batch, computed on the
+ * device from the packed records (Sec. II: a detector is the XOR of a face's
+ * outcome with its previous round's; the final data readout closes each Z
+ * face; Z_L is the parity of the top row of data qubits), then copied to
+ * caller-owned host memory (synchronises).  h_det: [shots][ceil(n_det/8)]
+ * bytes, detector i of a shot in byte i/8, bit i%8; h_logical: [shots] bytes
+ * (0/1).  Either may be NULL.  Errors: STN_EINVAL without a batch. */
+stn_status stn_read_detectors(stn_ctx *ctx, uint8_t *h_det, uint8_t *h_logical);
+
+/* Host-only: the detector table of `cfg`.  h_counts[2] = {n_det, n_logical};
+ * h_det (or NULL): [n_det][6] record indices whose XOR is the detector, -1
+ * padded; h_logical (or NULL): [n_logical] record indices of Z_L. */
+stn_status stn_compile_detectors(const stn_config *cfg, int32_t *h_counts, int32_t *h_det,
+                                 int32_t *h_logical);
+
 /* Algorithmic FLOPs of all MPS work since creation, summed over shot slots
  * (synchronises): textbook counts of the GEMMs, Householder R factors and
  * SVDs the sweeps perform (Sec. IV B), independent of the kernels' actual

@@ -54,6 +54,7 @@ class Simulator:
         self.n_meas = self.lib.stn_num_meas(ctx)
         self.n_events = self.lib.stn_num_events(ctx)
         self.n_ops = self.lib.stn_num_ops(ctx)
+        self.n_det = self.lib.stn_num_detectors(ctx)
         self.rounds = workload.rounds
         self.rec_bytes = (self.n_meas + 7) // 8
         self.words = (self.n_qubits + 63) // 64
@@ -111,6 +112,14 @@ class Simulator:
             out["discarded"] = np.array([x.discarded for x in s])
             out["logp"] = np.array([x.logp for x in s])
         return out
+
+    def read_detectors(self):
+        """Detector bits [shots][n_det] and Z_L parities [shots] of the batch,
+        computed on the device from its records."""
+        det = np.zeros((self.shots, (self.n_det + 7) // 8), dtype=np.uint8)
+        obs = np.zeros(self.shots, dtype=np.uint8)
+        self._check(self.lib.stn_read_detectors(self.ctx, _ptr(det), _ptr(obs)))
+        return unpack_records(det, self.n_det), obs
 
     def algorithmic_flops(self):
         v = ctypes.c_double()
@@ -181,6 +190,23 @@ def compile_program(workload):
     return counts, ops, pairs[: counts[1]]
 
 
+def compile_detectors(workload):
+    """Host-only detector table (no GPU): (det[n_det, 6] record indices, -1
+    padded, whose XOR is each detector; logical[n] record indices of Z_L)."""
+    lib = load()
+    cfg = config_from_workload(workload)
+    counts = np.zeros(2, dtype=np.int32)
+    st = lib.stn_compile_detectors(ctypes.byref(cfg), _ptr(counts), None, None)
+    if st != STN_OK:
+        raise StnError(st, "stn_compile_detectors failed")
+    det = np.zeros((counts[0], 6), dtype=np.int32)
+    logical = np.zeros(counts[1], dtype=np.int32)
+    st = lib.stn_compile_detectors(ctypes.byref(cfg), _ptr(counts), _ptr(det), _ptr(logical))
+    if st != STN_OK:
+        raise StnError(st, "stn_compile_detectors failed")
+    return det, logical
+
+
 def unpack_records(rec, n_meas):
     bits = np.unpackbits(rec, axis=1, bitorder="little")
     return bits[:, :n_meas].astype(np.uint8)
@@ -207,4 +233,4 @@ def dense_svd(precision, m, n, d_c, d_v, d_sig2, in_shared, stream=0):
 
 
 __all__ = ["Simulator", "StnError", "build", "load", "philox_uniforms", "unpack_records",
-           "config_from_workload", "compile_program", "dense_qr", "dense_svd"]
+           "config_from_workload", "compile_program", "compile_detectors", "dense_qr", "dense_svd"]

@@ -97,6 +97,10 @@ EXPORTS = [
     ("stn_read_records", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p]),
     ("stn_device_records", ctypes.c_void_p, [ctypes.c_void_p]),
+    ("stn_num_detectors", ctypes.c_int32, [ctypes.c_void_p]),
+    ("stn_read_detectors", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("stn_compile_detectors", ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p]),
     ("stn_algorithmic_flops", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("stn_profile_counters", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("stn_read_tableau", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,

@@ -38,7 +38,8 @@ struct stn_ctx {
       *d_status = nullptr;
   double *d_logp = nullptr, *d_disc = nullptr, *d_born = nullptr, *d_flops = nullptr;
   double *d_prof = nullptr;
-  uint8_t *d_rec = nullptr;
+  uint8_t *d_rec = nullptr, *d_det = nullptr, *d_obs = nullptr;
+  int32_t *d_det_table = nullptr, *d_logical = nullptr;
   void *d_scratch = nullptr;
   int *d_err = nullptr;
   std::string last_error;
@@ -209,6 +210,10 @@ stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_strea
   A(dalloc(c, &c->d_flops, sizeof(double) * S));
   A(dalloc(c, &c->d_prof, sizeof(double) * S * stn::kProfSlots));
   A(dalloc(c, &c->d_rec, static_cast<size_t>(S) * c->rec_bytes));
+  A(dalloc(c, &c->d_det, static_cast<size_t>(S) * ((c->prog.n_det + 7) / 8)));
+  A(dalloc(c, &c->d_obs, static_cast<size_t>(S)));
+  A(dalloc(c, &c->d_det_table, sizeof(int32_t) * c->prog.det.size()));
+  A(dalloc(c, &c->d_logical, sizeof(int32_t) * c->prog.logical.size()));
   A(dalloc(c, &c->d_scratch, c->elem * static_cast<size_t>(c->grid) * c->plan.total));
   A(dalloc(c, &c->d_err, sizeof(int)));
   if (!ok) {
@@ -223,6 +228,12 @@ stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_strea
                         cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->d_chimax, c->chimax.data(), sizeof(int) * (n + 1),
+                        cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_det_table, c->prog.det.data(), sizeof(int32_t) * c->prog.det.size(),
+                        cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_logical, c->prog.logical.data(), sizeof(int32_t) * c->prog.logical.size(),
                         cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_flops, 0, sizeof(double) * S, c->stream);
@@ -287,6 +298,20 @@ stn_status stn_compile_program(const stn_config *cfg, int32_t *h_counts, int32_t
     h_counts[4] = static_cast<int32_t>(prog.ops.size());
   }
   dump_program(prog, h_ops, h_pairs);
+  return STN_OK;
+}
+
+stn_status stn_compile_detectors(const stn_config *cfg, int32_t *h_counts, int32_t *h_det,
+                                 int32_t *h_logical) {
+  if (!validate(cfg).empty()) return STN_EINVAL;
+  stn::Program prog;
+  if (!stn::build_program(cfg->distance, cfg->rounds, cfg->pair_rule, prog).empty()) return STN_EINVAL;
+  if (h_counts) {
+    h_counts[0] = prog.n_det;
+    h_counts[1] = static_cast<int32_t>(prog.logical.size());
+  }
+  if (h_det) std::copy(prog.det.begin(), prog.det.end(), h_det);
+  if (h_logical) std::copy(prog.logical.begin(), prog.logical.end(), h_logical);
   return STN_OK;
 }
 
@@ -367,6 +392,26 @@ stn_status stn_read_records(stn_ctx *c, uint8_t *h_records, double *h_born,
 }
 
 const uint8_t *stn_device_records(const stn_ctx *c) { return c ? c->d_rec : nullptr; }
+
+int32_t stn_num_detectors(const stn_ctx *c) { return c ? c->prog.n_det : -1; }
+
+stn_status stn_read_detectors(stn_ctx *c, uint8_t *h_det, uint8_t *h_logical) {
+  if (!c) return STN_EINVAL;
+  if (c->shots < 1) return fail(c, STN_EINVAL, "no batch");
+  cudaError_t e = stn::launch_detectors(c->d_rec, c->rec_bytes, c->shots, c->d_det_table, c->prog.n_det,
+                                        c->d_logical, static_cast<int>(c->prog.logical.size()), c->d_det,
+                                        c->d_obs, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "detector kernel");
+  stn_status st = stn_sync(c);
+  if (st != STN_OK) return st;
+  if (h_det)
+    e = cudaMemcpy(h_det, c->d_det, static_cast<size_t>(c->shots) * ((c->prog.n_det + 7) / 8),
+                   cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && h_logical)
+    e = cudaMemcpy(h_logical, c->d_obs, static_cast<size_t>(c->shots), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stn_read_detectors");
+  return STN_OK;
+}
 
 stn_status stn_algorithmic_flops(stn_ctx *c, double *h_total) {
   if (!c || !h_total) return STN_EINVAL;

@@ -1775,6 +1775,49 @@ cudaError_t launch_dense_check(int precision, int what, int m, int n, void *A, v
                         : launch_dense_check_t<float>(what, m, n, A, V, sig2, use_smem, s);
 }
 
+// ---------------------------------------------------------------------------
+// Detector bits and the Z_L parity of every shot from its packed record: one
+// thread per (shot, detector byte), the last slot of a shot computing Z_L.
+__global__ void detector_kernel(const uint8_t *rec, int rec_bytes, int64_t shots, const int32_t *det,
+                                int n_det, const int32_t *logical, int n_logical, uint8_t *out_det,
+                                uint8_t *out_obs) {
+  const int det_bytes = (n_det + 7) / 8;
+  const int64_t total = shots * (det_bytes + 1);
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t shot = e / (det_bytes + 1);
+    const int j = static_cast<int>(e % (det_bytes + 1));
+    const uint8_t *r = rec + shot * rec_bytes;
+    if (j < det_bytes) {
+      unsigned v = 0;
+      for (int b = 0; b < 8 && j * 8 + b < n_det; ++b) {
+        const int32_t *row = det + (j * 8 + b) * kDetWidth;
+        unsigned par = 0;
+        for (int k = 0; k < kDetWidth; ++k)
+          if (row[k] >= 0) par ^= (r[row[k] >> 3] >> (row[k] & 7)) & 1u;
+        v |= par << b;
+      }
+      out_det[shot * det_bytes + j] = static_cast<uint8_t>(v);
+    } else {
+      unsigned par = 0;
+      for (int k = 0; k < n_logical; ++k) par ^= (r[logical[k] >> 3] >> (logical[k] & 7)) & 1u;
+      out_obs[shot] = static_cast<uint8_t>(par);
+    }
+  }
+}
+
+cudaError_t launch_detectors(const uint8_t *records, int rec_bytes, int64_t shots, const int32_t *det,
+                             int n_det, const int32_t *logical, int n_logical, uint8_t *out_det,
+                             uint8_t *out_obs, cudaStream_t s) {
+  const int64_t total = shots * ((n_det + 7) / 8 + 1);
+  if (total <= 0) return cudaSuccess;
+  int grid = static_cast<int>((total + 255) / 256);
+  if (grid > 4096) grid = 4096;
+  detector_kernel<<<grid, 256, 0, s>>>(records, rec_bytes, shots, det, n_det, logical, n_logical, out_det,
+                                       out_obs);
+  return cudaGetLastError();
+}
+
 int svd_smem_elems(int precision) { return precision == 0 ? SvdSmem<double>::elems : SvdSmem<float>::elems; }
 
 // ---------------------------------------------------------------------------

@@ -68,6 +68,9 @@ cudaError_t launch_round(int precision, const EngineParams &p, int grid, cudaStr
 cudaError_t launch_dense_check(int precision, int what, int m, int n, void *A, void *V, void *sig2,
                                int use_smem, cudaStream_t s);
 int svd_smem_elems(int precision);
+cudaError_t launch_detectors(const uint8_t *records, int rec_bytes, int64_t shots, const int32_t *det,
+                             int n_det, const int32_t *logical, int n_logical, uint8_t *out_det,
+                             uint8_t *out_obs, cudaStream_t s);
 cudaError_t launch_philox(uint64_t seed, uint64_t shot_offset, int64_t n_shots,
                           uint32_t event_offset, int n_events, double *out, cudaStream_t s);
 

@@ -14,6 +14,7 @@
 #include "program.h"
 
 #include <algorithm>
+#include <initializer_list>
 #include <map>
 #include <tuple>
 
@@ -141,6 +142,39 @@ std::string build_program(int d, int rounds, int pair_rule, Program &P) {
   P.seg_begin.push_back(static_cast<int>(P.ops.size()));
   P.n_events = ev;
   P.n_meas = rec;
+
+  // Detectors (Sec. II): round 0 sees only the Z faces, which start in a
+  // definite state; from round 1 on every face is compared with its previous
+  // outcome; the final data readout closes each Z face with its last round.
+  const int na = static_cast<int>(P.anc.size());
+  auto add_det = [&](std::initializer_list<int> idx, const std::vector<int> &more) {
+    int k = 0;
+    for (int i : idx) P.det.push_back(i), ++k;
+    for (int i : more) P.det.push_back(i), ++k;
+    for (; k < kDetWidth; ++k) P.det.push_back(-1);
+    ++P.n_det;
+  };
+  const std::vector<int> none;
+  for (int r = 0; r < rounds; ++r)
+    for (int ai = 0; ai < na; ++ai) {
+      if (r == 0) {
+        if (P.kind[P.anc[ai]] == 'Z') add_det({ai}, none);
+      } else {
+        add_det({r * na + ai, (r - 1) * na + ai}, none);
+      }
+    }
+  std::vector<int> data_pos(P.n, -1);
+  for (size_t i = 0; i < P.data.size(); ++i) data_pos[P.data[i]] = rounds * na + static_cast<int>(i);
+  for (int ai = 0; ai < na; ++ai) {
+    if (P.kind[P.anc[ai]] != 'Z') continue;
+    std::vector<int> dq;
+    for (int l = 0; l < 4; ++l)
+      if (P.slots[4 * ai + l] >= 0) dq.push_back(data_pos[P.slots[4 * ai + l]]);
+    add_det({(rounds - 1) * na + ai}, dq);
+  }
+  // Z_L: the data qubits of the top row (y = 1)
+  for (int q : P.data)
+    if (P.xy[2 * q + 1] == 1) P.logical.push_back(data_pos[q]);
   return std::string();
 }
 

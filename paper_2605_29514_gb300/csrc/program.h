@@ -43,7 +43,14 @@ struct Program {
   std::vector<Op> ops;
   std::vector<int> seg_begin;   // rounds + 2 entries: segment r = [seg_begin[r], seg_begin[r+1])
   int n_events = 0, n_meas = 0;
+  // Detectors of the Z-memory experiment: [n_det][kDetWidth] record indices
+  // whose XOR is the detector bit (-1 pads); logical: record indices of the
+  // final data readout whose XOR is the Z_L parity.
+  std::vector<int32_t> det, logical;
+  int n_det = 0;
 };
+
+constexpr int kDetWidth = 6;
 
 // Builds the program; returns an empty string or the reason for failure.
 std::string build_program(int d, int rounds, int pair_rule, Program &out);

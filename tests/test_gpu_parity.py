@@ -176,3 +176,19 @@ def test_d5_first_round_parity():
         rb = np.array(ref.born[:upto])
         err = np.abs(out["born"][s][:upto] - rb) / np.maximum(rb, 1e-4)
         assert np.all(err < 1e-5), f"shot {s}: max rel Born error {err.max():.3e} at record {int(err.argmax())}"
+
+
+def test_detectors_and_logical_on_device():
+    """Detector bits and Z_L parities computed on the device equal the
+    oracle's functions of the same records, bit for bit (noisy d=3 and d=5)."""
+    from oracle.circuit import detectors, logical_z
+    for w, shots in [(D3_EXACT.with_(p=0.02), 16), (D5_BENCH.with_(rounds=1, chi_cap=16), 4)]:
+        sim, out, _ = gpu_run(w, shots)
+        det, obs = sim.read_detectors()
+        prog = make_program(w)
+        assert det.shape == (shots, sim.n_det)
+        for s in range(shots):
+            rec = list(out["bits"][s])
+            assert list(det[s]) == detectors(prog, rec)
+            assert int(obs[s]) == logical_z(prog, rec)
+        sim.close()

@@ -89,3 +89,20 @@ def test_invalid_configs_rejected(lib, bad):
     with pytest.raises(stn.StnError) as e:
         stn.compile_program(D3_EXACT.with_(**bad))
     assert e.value.status == stn.STN_EINVAL
+
+
+@pytest.mark.parametrize("w", [D3_EXACT, D5_BENCH, D3_EXACT.with_(rounds=1), D5_BENCH.with_(distance=7, rounds=2)])
+def test_detector_table_matches_oracle(lib, w):
+    """The compiled detector table, applied to arbitrary records, gives the
+    oracle's detector bits and Z_L parity (Sec. II)."""
+    from oracle.circuit import detectors, logical_z
+    det, logical = stn.compile_detectors(w)
+    prog = make_program(w)
+    rng = np.random.default_rng(w.distance * 10 + w.rounds)
+    n_meas = w.n_meas
+    for _ in range(8):
+        rec = rng.integers(0, 2, size=n_meas)
+        ext = np.append(rec, 0)  # index -1 reads the appended zero
+        got = np.bitwise_xor.reduce(ext[det], axis=1)
+        assert list(got) == detectors(prog, list(rec))
+        assert int(np.bitwise_xor.reduce(rec[logical])) == logical_z(prog, list(rec))
