@@ -184,6 +184,7 @@ def main():
         return
     import torch
     import paper_2605_29514_gb300 as stn
+    from paper_2605_29514_gb300.shards import rank_base
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -204,7 +205,7 @@ def main():
     d_theta = torch.empty_like(th_host, device="cuda")
     d_theta.copy_(th_host)
     rec_host = torch.empty((B, sim.rec_bytes), dtype=torch.uint8).pin_memory()
-    base = rank * 10 ** 9  # disjoint shot ranges per rank
+    base = rank_base(rank)  # disjoint global shot ranges per rank
 
     # warm-up: W steps, each the first segment (syndrome round 0) of a fresh batch
     for i in range(W):

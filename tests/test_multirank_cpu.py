@@ -1,0 +1,87 @@
+"""The multi-rank path on CPU ranks (gloo, world size 2): shards partition the
+shots, a shard's records are those of the same global shot indices in one
+process (counter-based Philox draws), and the summed tallies of a sharded job
+equal the single-process tallies."""
+
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_2605_29514_gb300.shards import allreduce_sum, rank_base, shard
+
+torch = pytest.importorskip("torch")
+
+
+def test_shards_partition():
+    for total in [0, 1, 7, 16384, 100001]:
+        for world in [1, 2, 3, 8]:
+            got = [shard(total, world, r) for r in range(world)]
+            assert sum(c for _, c in got) == total
+            nxt = 0
+            for lo, c in got:
+                assert lo == nxt and c >= 0
+                nxt = lo + c
+    assert rank_base(1) - rank_base(0) >= 10 ** 9
+    with pytest.raises(ValueError):
+        shard(10, 2, 2)
+
+
+def tallies(w, first, count):
+    from oracle.circuit import detectors, logical_z
+    from oracle.shot import make_program, run_shot
+    from workloads import theta_table
+    prog = make_program(w)
+    theta = theta_table(w, len(prog.pairs))
+    det_counts = None
+    flips = 0
+    logp = 0.0
+    for s in range(first, first + count):
+        res = run_shot(w, s, theta, prog)
+        d = np.array(detectors(prog, res.record), dtype=np.float64)
+        det_counts = d if det_counts is None else det_counts + d
+        flips += logical_z(prog, res.record)
+        logp += res.logp
+    return det_counts, np.array([flips, logp, count], dtype=np.float64)
+
+
+def _worker(rank, world, port, w, total, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    first, count = shard(total, world, rank)
+    det, misc = tallies(w, first, count)
+    det, misc = allreduce_sum([det, misc], dist)
+    if rank == 0:
+        q.put((det.tolist(), misc.tolist()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_sharded_tallies_equal_single_process():
+    import multiprocessing as mp
+    from workloads import D3_EXACT
+    w = D3_EXACT.with_(rounds=1, p=0.05, chi_cap=8)
+    total, world = 6, 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, w, total, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    det, misc = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    det1, misc1 = tallies(w, 0, total)
+    assert np.array_equal(np.array(det), det1)
+    assert misc[0] == misc1[0] and misc[2] == total
+    assert abs(misc[1] - misc1[1]) < 1e-9 * max(1.0, abs(misc1[1]))

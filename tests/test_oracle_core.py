@@ -223,3 +223,22 @@ def test_keep_count_rules():
     assert keep_count(s, 4, 0.0, 1e-12) == 2
     # cap right after the cluster keeps it
     assert keep_count(s, 5, 0.0, 1e-12) == 5
+
+
+def test_oracle_matches_its_stored_records():
+    """Regression guard: the oracle still produces the records and Born
+    probabilities stored by tests/golden/make_oracle_golden.py (a change to
+    the oracle's arithmetic must regenerate them and say why)."""
+    import os
+    from oracle.shot import make_program, run_shot
+    from workloads import D3_EXACT, theta_table
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_d3_records.txt")
+    rows = [l.split() for l in open(path) if not l.startswith("#")]
+    w = D3_EXACT
+    prog = make_program(w)
+    theta = theta_table(w, len(prog.pairs))
+    for row in rows:
+        s, bits, born = int(row[0]), row[1], np.array([float(x) for x in row[2:]])
+        res = run_shot(w, s, theta, prog)
+        assert "".join(str(b) for b in res.record) == bits
+        assert np.abs(np.array(res.born) - born).max() < 1e-13
