@@ -225,6 +225,29 @@ stn_status stn_dense_qr(int32_t precision, int32_t m, int32_t n, void *d_b, void
 stn_status stn_dense_svd(int32_t precision, int32_t m, int32_t n, void *d_c, void *d_v, void *d_sig2,
                          int32_t in_shared, void *cuda_stream);
 
+/* Allocation-free variant of stn_dense_svd with in_shared = 3 (the large-bond
+ * SVD of the truncation sweep).  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they need
+ * the decomposition (a host callback, a framework pool that forbids cudaMalloc
+ * while work is queued, an embedded runtime that owns every buffer).  It
+ * allocates nothing, neither through the CUDA runtime nor any library: its
+ * work copy of the input lives in one static device array of 1 MiB per GPU,
+ * held from library load until process exit.
+ *   d_c: input, ROW-major m x n complex of the precision (device), left
+ *        unchanged.  d_v (n x n, column-major), d_sig2[n]: outputs as for
+ *        stn_dense_svd with in_shared = 3.  m <= 1024.
+ *   Limit: m n complex elements must fit 1 MiB (m n <= 131072 for
+ *   complex64, 65536 for complex128); larger requests return STN_EOVERFLOW
+ *   and launch nothing.  Errors: STN_EINVAL for bad sizes or null pointers,
+ *   STN_ECUDA for a runtime failure.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture begins.  Every call shares the array and it keeps the last call's
+ * contents; calls that overlap on the GPU race on it, so callers must order
+ * them (one stream, or events between streams). */
+stn_status stn_dense_svd_noalloc(int32_t precision, int32_t m, int32_t n, const void *d_c, void *d_v,
+                                 void *d_sig2, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

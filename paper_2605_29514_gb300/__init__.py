@@ -232,5 +232,15 @@ def dense_svd(precision, m, n, d_c, d_v, d_sig2, in_shared, stream=0):
         raise StnError(st, "stn_dense_svd failed")
 
 
+def dense_svd_noalloc(precision, m, n, d_c, d_v, d_sig2, stream=0):
+    """stn_dense_svd_noalloc: the large-bond SVD with no device allocation
+    (its work copy lives in the library's static 1 MiB array); d_c is kept."""
+    st = load().stn_dense_svd_noalloc(int(precision), int(m), int(n), ctypes.c_void_p(d_c),
+                                      ctypes.c_void_p(d_v), ctypes.c_void_p(d_sig2), ctypes.c_void_p(stream))
+    if st != STN_OK:
+        raise StnError(st, "stn_dense_svd_noalloc failed")
+
+
 __all__ = ["Simulator", "StnError", "build", "load", "philox_uniforms", "unpack_records",
-           "config_from_workload", "compile_program", "compile_detectors", "dense_qr", "dense_svd"]
+           "config_from_workload", "compile_program", "compile_detectors", "dense_qr", "dense_svd",
+           "dense_svd_noalloc"]

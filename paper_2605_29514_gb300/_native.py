@@ -115,6 +115,8 @@ EXPORTS = [
                                     ctypes.c_void_p]),
     ("stn_dense_svd", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    ("stn_dense_svd_noalloc", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("stn_philox_uniforms", ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                            ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p,
                                            ctypes.c_void_p]),

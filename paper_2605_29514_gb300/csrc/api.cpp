@@ -499,6 +499,19 @@ stn_status stn_dense_svd(int32_t precision, int32_t m, int32_t n, void *d_c, voi
   return e == cudaSuccess ? STN_OK : STN_ECUDA;
 }
 
+stn_status stn_dense_svd_noalloc(int32_t precision, int32_t m, int32_t n, const void *d_c, void *d_v,
+                                 void *d_sig2, void *cuda_stream) {
+  if ((precision != 0 && precision != 1) || m < 1 || n < 1 || m > 1024 || !d_c || !d_v || !d_sig2)
+    return STN_EINVAL;
+  if (2 * m + 4 > stn::svd_smem_elems(precision) || 2 * n + 4 > stn::svd_smem_elems(precision))
+    return STN_EINVAL;
+  const size_t elem = precision == 0 ? 16 : 8;
+  if (static_cast<size_t>(m) * n * elem > stn::noalloc_scratch_bytes()) return STN_EOVERFLOW;
+  cudaError_t e = stn::launch_svd_noalloc(precision, m, n, d_c, d_v, d_sig2,
+                                          static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? STN_OK : STN_ECUDA;
+}
+
 stn_status stn_philox_uniforms(uint64_t seed, uint64_t shot_offset, int64_t n_shots,
                                uint32_t event_offset, int32_t n_events, double *d_out,
                                void *cuda_stream) {

@@ -68,6 +68,9 @@ cudaError_t launch_round(int precision, const EngineParams &p, int grid, cudaStr
 cudaError_t launch_dense_check(int precision, int what, int m, int n, void *A, void *V, void *sig2,
                                int use_smem, cudaStream_t s);
 int svd_smem_elems(int precision);
+size_t noalloc_scratch_bytes();
+cudaError_t launch_svd_noalloc(int precision, int m, int n, const void *C, void *V, void *sig2,
+                               cudaStream_t s);
 cudaError_t launch_detectors(const uint8_t *records, int rec_bytes, int64_t shots, const int32_t *det,
                              int n_det, const int32_t *logical, int n_logical, uint8_t *out_det,
                              uint8_t *out_obs, cudaStream_t s);
