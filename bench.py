@@ -250,9 +250,10 @@ def main():
     phases = {"segment_ms": [round(x, 3) for x in seg_ms],
               "cycle_share": {k.replace("_cycles", ""): round(dprof[k] / loop, 4)
                               for k in ("left_sweep_cycles", "svd_cycles", "right_sweep_rest_cycles",
-                                        "expectation_cycles")},
+                                        "expectation_cycles", "gauge_cycles")},
               "svds_per_shot": {"shared_memory": dprof["svd_count_shared"] / (B * (K // segs)),
-                                "large_bond": dprof["svd_count_large"] / (B * (K // segs))},
+                                "large_bond": dprof["svd_count_large"] / (B * (K // segs)),
+                                "gauge_sites": dprof["gauge_sites"] / (B * (K // segs))},
               "source": "stn_profile_counters: SM clock cycles of each CTA per phase, over the timed batches"}
     secs = ev0.elapsed_time(ev1) / 1000.0
     if pg:

@@ -167,13 +167,15 @@ stn_status stn_compile_detectors(const stn_config *cfg, int32_t *h_counts, int32
 stn_status stn_algorithmic_flops(stn_ctx *ctx, double *h_total);
 
 /* Phase counters of all round launches since creation, summed over shot
- * slots (synchronises).  h_out[8]: SM clock cycles spent by the CTAs in
+ * slots (synchronises).  h_out[10]: SM clock cycles spent by the CTAs in
  * [0] the left (R-factor) sweep, [1] the right sweep's SVDs, [2] the rest of
  * the right sweep (contractions, sorting, new sites), [3] expectation values,
- * [4] the whole op loop (so [4] - [0..3] is the tableau and bookkeeping);
- * then counts of [5] shared-memory SVDs and [6] large-bond SVDs (Householder
- * R factor plus Jacobi on R^dag); [7] is zero.  Diagnostics only: they
- * explain where a round's time goes, they are not part of the path. */
+ * [4] the whole op loop (so [4] - [0..3] - [7] is the tableau and
+ * bookkeeping); counts of [5] shared-memory SVDs and [6] large-bond SVDs
+ * (Householder R factor plus Jacobi on R^dag); [7] cycles of the gauge steps
+ * that move the orthogonality centre into an operator's support and [8] the
+ * number of sites they crossed; [9] is zero.  Diagnostics only: they explain
+ * where a round's time goes, they are not part of the path. */
 stn_status stn_profile_counters(stn_ctx *ctx, double *h_out);
 
 /* Inverse tableau of one shot of the current batch (synchronises): rows

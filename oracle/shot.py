@@ -11,8 +11,10 @@ Per op of the program (`oracle.circuit.build_program`):
     (control, target) over I, X, Y, Z, skipping II) non-identity Paulis.
   * Crosstalk exp(-i theta Q) (Eq. 4, sign reading exp(-i theta Q)):
     P' = C^dag Q C, then cos(theta) I - i sin(theta) P' on the MPS as a
-    bond-2 MPO, then compression (Sec. IV B) over the support of P' widened
-    to include the orthogonality centre (`sweep_span`).
+    bond-2 MPO, then compression (Sec. IV B) over the support [lo, hi] of P'
+    (`prepare_span`: the orthogonality centre is first moved into [lo, hi]
+    by exact QR gauge steps, so only the bonds the MPO doubled are
+    truncated).
   * Z measurement of qubit q (Sec. IV A: a Pauli pushed through C and applied
     to the tensor network): P' = C^dag Z_q C, e = <phi|P'|phi>,
     p0 = (1 + e)/2, outcome b = 0 iff u < p0.
@@ -136,14 +138,15 @@ class ShotSim:
             self.T.left_pauli("X", [q])
 
     # -- non-Clifford and measurement ------------------------------------------
-    def sweep_span(self, lo, hi):
-        """Sites swept by the compression after an operator on [lo, hi]: the
-        support plus every site up to the orthogonality centre, so that the
-        sites left of the sweep are left-canonical and those right of it
-        right-canonical (Sec. IV B leaves the sweep extent open; covering the
-        centre replaces separate gauge moves)."""
-        c = self.mps.center
-        return min(lo, c), max(hi, c)
+    def prepare_span(self, lo, hi):
+        """Sites swept by the compression after an operator on [lo, hi].
+        Sec. IV B truncates the bonds the operator's MPO enlarged, and leaves
+        the rest of the sweep open; here the orthogonality centre is moved
+        into [lo, hi] first by exact QR gauge steps (no truncation), so the
+        sites left of lo are left-canonical, those right of hi
+        right-canonical, and the sweep covers exactly the support."""
+        self.mps.move_center_into(lo, hi)
+        return lo, hi
 
     def rotation(self, k):
         pair = self.prog.pairs[k]
@@ -157,7 +160,7 @@ class ShotSim:
         th = float(self.theta[k])
         supp = pp.support()
         lo, hi = int(supp.min()), int(supp.max())
-        a, b = self.sweep_span(lo, hi)
+        a, b = self.prepare_span(lo, hi)
         ops1 = {int(s): pp.site_matrix(s) for s in supp}
         w1 = -1j * math.sin(th) * (1j ** pp.m)
         self.mps.apply_two_branch(lo, hi, {}, ops1, math.cos(th), w1)
@@ -178,7 +181,7 @@ class ShotSim:
         pb = p0 if b == 0 else 1.0 - p0
         self.born[rec] = pb
         self.logp += math.log(pb) if pb > 0 else -math.inf
-        sa, sb = self.sweep_span(lo, hi)
+        sa, sb = self.prepare_span(lo, hi)
         if not pp.x.any():
             w1 = (1 if b == 0 else -1) * (1j ** pp.m) * 0.5
             self.mps.apply_two_branch(lo, hi, {}, ops, 0.5, w1)

@@ -127,14 +127,15 @@ class Simulator:
         return v.value
 
     PROFILE_KEYS = ("left_sweep_cycles", "svd_cycles", "right_sweep_rest_cycles", "expectation_cycles",
-                    "op_loop_cycles", "svd_count_shared", "svd_count_large")
+                    "op_loop_cycles", "svd_count_shared", "svd_count_large", "gauge_cycles",
+                    "gauge_sites")
 
     def profile_counters(self):
         """Per-phase SM cycles and SVD counts summed over shot slots since
         creation (see stn_profile_counters)."""
-        buf = (ctypes.c_double * 8)()
+        buf = (ctypes.c_double * 10)()
         self._check(self.lib.stn_profile_counters(self.ctx, ctypes.cast(buf, ctypes.c_void_p)))
-        return dict(zip(self.PROFILE_KEYS, list(buf)[:7]))
+        return dict(zip(self.PROFILE_KEYS, list(buf)[:9]))
 
     def read_records_into(self, h_records_ptr):
         """Packed records of the batch into caller-owned host memory

@@ -253,12 +253,52 @@ __device__ __forceinline__ T warp_sum(T v) {
 // m nb + 2 nb^2 complex elements (nb is reduced to fit).  CTA-wide.
 constexpr int kQrPanel = 16;
 
-template <typename T>
-__device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *pbuf, int pbuf_elems, double *red,
-                             double *dm) {
-  const int steps = min(m, n);
+__device__ __forceinline__ int qr_panel_width(int m, int pbuf_elems) {
   int nb = kQrPanel;
   while (nb > 1 && static_cast<int64_t>(m) * nb + 2 * nb * nb > pbuf_elems) --nb;
+  return nb;
+}
+
+// T of the compact WY form of a panel's reflectors (columns of Vp, row-major
+// [mr][nb], u_b zero above row b): T upper triangular, T_kk = 2,
+// T[0:k, k] = -2 T[0:k, 0:k] (V[:, 0:k]^dag u_k).  G is scratch.  CTA-wide.
+template <typename T>
+__device__ void wy_t_factor(int mr, int jb, int nb, const cplx<T> *Vp, cplx<T> *Tm, cplx<T> *G) {
+  for (int pr = warp_id(); pr < jb * jb; pr += kWarps) {
+    const int a = pr / jb, b = pr % jb;
+    if (a >= b) continue;
+    T gr = 0, gi = 0;
+    for (int i = b + lane_id(); i < mr; i += 32) {  // u_b vanishes above row b
+      const cplx<T> x = Vp[i * nb + a], y = Vp[i * nb + b];
+      gr += x.re * y.re + x.im * y.im;
+      gi += x.re * y.im - x.im * y.re;
+    }
+    gr = warp_sum(gr);
+    gi = warp_sum(gi);
+    if (lane_id() == 0) G[a * nb + b] = cmake<T>(gr, gi);
+  }
+  __syncthreads();
+  if (tid() == 0) {
+    for (int k = 0; k < jb; ++k) {
+      Tm[k * nb + k] = cmake<T>(2, 0);
+      for (int a = 0; a < k; ++a) {
+        cplx<T> acc = cmake<T>(0, 0);
+        for (int b = a; b < k; ++b) cfma(acc, Tm[a * nb + b], G[b * nb + k]);
+        Tm[a * nb + k] = cscale(acc, T(-2));
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// With vstore (row-major m x min(m,n)), the reflectors are also kept there
+// (column j holds u_j in rows j..m-1; rows above are not written) so that
+// form_q can build Q explicitly.
+template <typename T>
+__device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *pbuf, int pbuf_elems, double *red,
+                             double *dm, cplx<T> *vstore = nullptr) {
+  const int steps = min(m, n);
+  const int nb = qr_panel_width(m, pbuf_elems);
   cplx<T> *Vp = pbuf;                                   // [(m - j0)][nb], row-major
   cplx<T> *Tm = pbuf + static_cast<int64_t>(m) * nb;  // [nb][nb]
   cplx<T> *G = Tm + nb * nb;                            // [nb][nb], G[a][b] = u_a^dag u_b
@@ -326,33 +366,16 @@ __device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *pbuf, in
       }
       __syncthreads();
     }
-    if (j0 + jb >= n) continue;  // no trailing columns
-    // G (strictly upper part), then T by its column recursion
-    for (int pr = warp_id(); pr < jb * jb; pr += kWarps) {
-      const int a = pr / jb, b = pr % jb;
-      if (a >= b) continue;
-      T gr = 0, gi = 0;
-      for (int i = b + lane_id(); i < mr; i += 32) {  // u_b vanishes above row b
-        const cplx<T> x = Vp[i * nb + a], y = Vp[i * nb + b];
-        gr += x.re * y.re + x.im * y.im;
-        gi += x.re * y.im - x.im * y.re;
+    if (vstore != nullptr)
+      for (int e = tid(); e < mr * jb; e += kThreads) {
+        const int i = e / jb, c = e % jb;
+        vstore[static_cast<int64_t>(j0 + i) * steps + j0 + c] = Vp[i * nb + c];
       }
-      gr = warp_sum(gr);
-      gi = warp_sum(gi);
-      if (lane_id() == 0) G[a * nb + b] = cmake<T>(gr, gi);
+    if (j0 + jb >= n) {  // no trailing columns
+      __syncthreads();
+      continue;
     }
-    __syncthreads();
-    if (tid() == 0) {
-      for (int k = 0; k < jb; ++k) {
-        Tm[k * nb + k] = cmake<T>(2, 0);
-        for (int a = 0; a < k; ++a) {
-          cplx<T> acc = cmake<T>(0, 0);
-          for (int b = a; b < k; ++b) cfma(acc, Tm[a * nb + b], G[b * nb + k]);
-          Tm[a * nb + k] = cscale(acc, T(-2));
-        }
-      }
-    }
-    __syncthreads();
+    wy_t_factor<T>(mr, jb, nb, Vp, Tm, G);
     // trailing columns: b <- b - V (T^dag (V^dag b))
     for (int c = j0 + jb + tid(); c < n; c += kThreads) {
       cplx<T> w[kQrPanel];
@@ -383,6 +406,67 @@ __device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *pbuf, in
             acc = cmake<T>(acc.re - t.re, acc.im - t.im);
           }
         bref = acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Explicit Q (m x steps, row-major) of a Householder QR whose reflectors
+// qr_r_inplace kept in vstore: Q = P_1 ... P_steps [I; 0], built panel by
+// panel from the last, each panel applied as I - V T V^dag to the columns at
+// or right of it (the columns left of panel p are unit vectors its
+// reflectors do not touch).  Same shared-memory needs as qr_r_inplace.
+template <typename T>
+__device__ void form_q(int m, int steps, const cplx<T> *vstore, cplx<T> *Q, cplx<T> *pbuf, int pbuf_elems) {
+  const int nb = qr_panel_width(m, pbuf_elems);
+  cplx<T> *Vp = pbuf;
+  cplx<T> *Tm = pbuf + static_cast<int64_t>(m) * nb;
+  cplx<T> *G = Tm + nb * nb;
+  for (int64_t e = tid(); e < static_cast<int64_t>(m) * steps; e += kThreads) {
+    const int i = static_cast<int>(e / steps), c = static_cast<int>(e % steps);
+    Q[e] = cmake<T>(i == c ? T(1) : T(0), 0);
+  }
+  const int npan = (steps + nb - 1) / nb;
+  for (int p = npan - 1; p >= 0; --p) {
+    const int j0 = p * nb, jb = min(nb, steps - j0), mr = m - j0;
+    for (int e = tid(); e < mr * nb; e += kThreads) {
+      const int i = e / nb, c = e % nb;
+      // u_c is zero above its own row; rows above were never written
+      Vp[e] = (c < jb && i >= c) ? vstore[static_cast<int64_t>(j0 + i) * steps + j0 + c] : cmake<T>(0, 0);
+    }
+    __syncthreads();
+    wy_t_factor<T>(mr, jb, nb, Vp, Tm, G);
+    for (int c = j0 + tid(); c < steps; c += kThreads) {
+      cplx<T> w[kQrPanel];
+#pragma unroll
+      for (int k = 0; k < kQrPanel; ++k) w[k] = cmake<T>(0, 0);
+      for (int i = 0; i < mr; ++i) {
+        const cplx<T> q = Q[static_cast<int64_t>(j0 + i) * steps + c];
+#pragma unroll
+        for (int k = 0; k < kQrPanel; ++k)
+          if (k < jb) cfma(w[k], cconj(Vp[i * nb + k]), q);
+      }
+      // w <- T w in place, lowest index first: w'[a] = sum_{b>=a} T[a][b] w[b]
+#pragma unroll
+      for (int a = 0; a < kQrPanel; ++a) {
+        if (a >= jb) continue;
+        cplx<T> acc = cmake<T>(0, 0);
+#pragma unroll
+        for (int b = a; b < kQrPanel; ++b)
+          if (b < jb) cfma(acc, Tm[a * nb + b], w[b]);
+        w[a] = acc;
+      }
+      for (int i = 0; i < mr; ++i) {
+        cplx<T> &qref = Q[static_cast<int64_t>(j0 + i) * steps + c];
+        cplx<T> acc = qref;
+#pragma unroll
+        for (int k = 0; k < kQrPanel; ++k)
+          if (k < jb) {
+            const cplx<T> t = cmul(Vp[i * nb + k], w[k]);
+            acc = cmake<T>(acc.re - t.re, acc.im - t.im);
+          }
+        qref = acc;
       }
     }
     __syncthreads();
@@ -802,7 +886,7 @@ __host__ __device__ size_t smem_bytes(int n, int W, int svd_elems) {
   add(sizeof(int64_t) * (n + 2));     // off
   add(sizeof(int64_t) * (n + 2));     // goff
   add(sizeof(double) * kThreads);     // red
-  add(sizeof(double) * 16);           // dmisc
+  add(sizeof(double) * 24);           // dmisc
   add(sizeof(cplx<T>) * kBK * (kBM + kPad + kBN + kPad));  // tile
   add(sizeof(cplx<T>) * svd_elems);  // jbuf
   add(sizeof(cplx<T>) * kMaxVec);     // uvec
@@ -832,7 +916,7 @@ __device__ Smem<T> carve(char *base, int n, int W, int svd_elems) {
   s.off = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (n + 2)));
   s.goff = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (n + 2)));
   s.red = reinterpret_cast<double *>(take(sizeof(double) * kThreads));
-  s.dmisc = reinterpret_cast<double *>(take(sizeof(double) * 16));
+  s.dmisc = reinterpret_cast<double *>(take(sizeof(double) * 24));
   s.tile = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * kBK * (kBM + kPad + kBN + kPad)));
   s.jbuf = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * svd_elems));
   s.uvec = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * kMaxVec));
@@ -958,6 +1042,79 @@ __device__ int keep_count(const T *lam_sorted, int n, int cap, double cutoff, do
     k = kk < 1 ? 1 : kk;
   }
   return k;
+}
+
+// Exact gauge steps (no truncation) moving the orthogonality centre of a
+// shot's MPS from its current site to `target`, so that the sites left of an
+// operator's support are left-canonical and those right of it
+// right-canonical before the operator is applied (Sec. IV B).
+//   Right across site k: A_k as a (2 chi_k) x chi_{k+1} matrix = Q R
+//   (Householder); site k becomes Q (bond k+1 becomes min(2 chi_k,
+//   chi_{k+1})) and A_{k+1} <- R A_{k+1}.
+//   Left across site k: A_k^dag as a (2 chi_{k+1}) x chi_k matrix = Q R;
+//   site k becomes Q^dag and A_{k-1} <- A_{k-1} R^dag.
+template <typename T>
+__device__ void mps_move_center(const EngineParams &P, const Smem<T> &S, int64_t shot, const Scratch<T> &X,
+                                int target) {
+  int *chi = S.chi;
+  const cplx<T> one = cmake<T>(1, 0), zero = cmake<T>(0, 0);
+  int c = S.misc[M_CENTER];
+  while (c < target) {
+    const int l = chi[c], r = chi[c + 1], r2 = chi[c + 2];
+    const int m = 2 * l, steps = min(m, r);
+    if (m > kMaxVec) {
+      if (tid() == 0) S.misc[M_FAIL] = STN_EOVERFLOW;
+      __syncthreads();
+      return;
+    }
+    cplx<T> *A = site_ptr<T>(P, shot, c), *Bn = site_ptr<T>(P, shot, c + 1);
+    for (int e = tid(); e < m * r; e += kThreads) X.t[e] = A[e];
+    __syncthreads();
+    qr_r_inplace<T>(m, r, X.t, r, S.jbuf, P.svd_elems, S.red, S.dmisc + 4, X.h);
+    form_q<T>(m, steps, X.h, X.y, S.jbuf, P.svd_elems);
+    cgemm<T, 0, 0>(steps, 2 * r2, r, one, X.t, r, Bn, 2 * r2, zero, X.w, 2 * r2, S.tile);
+    for (int e = tid(); e < m * steps; e += kThreads) A[e] = X.y[e];
+    for (int e = tid(); e < steps * 2 * r2; e += kThreads) Bn[e] = X.w[e];
+    if (tid() == 0) {
+      chi[c + 1] = steps;
+      S.dmisc[D_FLOPS] += 2.0 * qr_flops(m, r) + gemm_flops(steps, 2 * r2, r);
+      S.dmisc[D_PROF + 1 + PROF_NGAUGE] += 1.0;
+    }
+    __syncthreads();
+    ++c;
+  }
+  while (c > target) {
+    const int l = chi[c], r = chi[c + 1], ll = chi[c - 1];
+    const int m = 2 * r, steps = min(m, l);
+    if (m > kMaxVec) {
+      if (tid() == 0) S.misc[M_FAIL] = STN_EOVERFLOW;
+      __syncthreads();
+      return;
+    }
+    cplx<T> *A = site_ptr<T>(P, shot, c), *Am = site_ptr<T>(P, shot, c - 1);
+    for (int e = tid(); e < m * l; e += kThreads) {
+      const int j = e / l, i = e % l;  // X.t[j][i] = conj(A[i][j]), A as l x 2r
+      X.t[e] = cconj(A[static_cast<int64_t>(i) * m + j]);
+    }
+    __syncthreads();
+    qr_r_inplace<T>(m, l, X.t, l, S.jbuf, P.svd_elems, S.red, S.dmisc + 4, X.h);
+    form_q<T>(m, steps, X.h, X.y, S.jbuf, P.svd_elems);
+    cgemm<T, 0, 1>(2 * ll, steps, l, one, Am, l, X.t, l, zero, X.w, steps, S.tile);
+    for (int e = tid(); e < steps * m; e += kThreads) {
+      const int k = e / m, j = e % m;
+      A[e] = cconj(X.y[static_cast<int64_t>(j) * steps + k]);
+    }
+    for (int e = tid(); e < 2 * ll * steps; e += kThreads) Am[e] = X.w[e];
+    if (tid() == 0) {
+      chi[c] = steps;
+      S.dmisc[D_FLOPS] += 2.0 * qr_flops(m, l) + gemm_flops(2 * ll, steps, l);
+      S.dmisc[D_PROF + 1 + PROF_NGAUGE] += 1.0;
+    }
+    __syncthreads();
+    --c;
+  }
+  if (tid() == 0) S.misc[M_CENTER] = target;
+  __syncthreads();
 }
 
 // Two phases of applying the two-branch MPO `spec` on [lo, hi] and
@@ -1562,8 +1719,9 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
             int c = S.misc[M_CENTER];
             S.misc[M_LO] = lo;
             S.misc[M_HI] = hi;
-            S.misc[M_A] = min(lo, c);
-            S.misc[M_B] = max(hi, c);
+            (void)c;
+            S.misc[M_A] = lo;
+            S.misc[M_B] = hi;
             S.misc[M_J] = j;
             S.misc[M_CASEB] = xany;
             S.misc[M_BIT] = m | ((((m - xz) & 3) == 2) << 4);  // phase | (sign < 0) << 4
@@ -1581,6 +1739,18 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
           __syncthreads();
           if (S.misc[M_FAIL]) break;
           const int a = S.misc[M_A], b = S.misc[M_B];
+          {
+            // the centre moves into [a, b] by exact gauge steps; the sweep
+            // then covers the operator's support only
+            const int c0 = S.misc[M_CENTER];
+            const int tgt = c0 < a ? a : (c0 > b ? b : c0);
+            if (tgt != c0) {
+              long long tg = clock64();
+              mps_move_center<T>(P, S, shot, X, tgt);
+              prof_mark(S.dmisc, PROF_GAUGE, tg);
+            }
+          }
+          if (S.misc[M_FAIL]) break;
           int caseB = 0, lidx = 0, outcome = 0;
           if (meas) {
             // The Born probability of the less likely branch is taken from the
