@@ -376,12 +376,24 @@ __device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *pbuf, in
       continue;
     }
     wy_t_factor<T>(mr, jb, nb, Vp, Tm, G);
-    // trailing columns: b <- b - V (T^dag (V^dag b))
+    // trailing columns: b <- b - V (T^dag (V^dag b)); rows go four at a
+    // time so that four loads per thread are in flight
     for (int c = j0 + jb + tid(); c < n; c += kThreads) {
       cplx<T> w[kQrPanel];
 #pragma unroll
       for (int k = 0; k < kQrPanel; ++k) w[k] = cmake<T>(0, 0);
-      for (int i = 0; i < mr; ++i) {
+      int i = 0;
+      for (; i + 4 <= mr; i += 4) {
+        cplx<T> b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) b[u] = B[static_cast<int64_t>(j0 + i + u) * ld + c];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int k = 0; k < kQrPanel; ++k)
+            if (k < jb) cfma(w[k], cconj(Vp[(i + u) * nb + k]), b[u]);
+      }
+      for (; i < mr; ++i) {
         const cplx<T> b = B[static_cast<int64_t>(j0 + i) * ld + c];
 #pragma unroll
         for (int k = 0; k < kQrPanel; ++k)
@@ -396,7 +408,22 @@ __device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *pbuf, in
         for (int b = 0; b <= a; ++b) cfma(acc, cconj(Tm[b * nb + a]), w[b]);
         w[a] = acc;
       }
-      for (int i = 0; i < mr; ++i) {
+      for (i = 0; i + 4 <= mr; i += 4) {
+        cplx<T> b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) b[u] = B[static_cast<int64_t>(j0 + i + u) * ld + c];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+          for (int k = 0; k < kQrPanel; ++k)
+            if (k < jb) {
+              const cplx<T> t = cmul(Vp[(i + u) * nb + k], w[k]);
+              b[u] = cmake<T>(b[u].re - t.re, b[u].im - t.im);
+            }
+          B[static_cast<int64_t>(j0 + i + u) * ld + c] = b[u];
+        }
+      }
+      for (; i < mr; ++i) {
         cplx<T> &bref = B[static_cast<int64_t>(j0 + i) * ld + c];
         cplx<T> acc = bref;
 #pragma unroll
@@ -441,7 +468,18 @@ __device__ void form_q(int m, int steps, const cplx<T> *vstore, cplx<T> *Q, cplx
       cplx<T> w[kQrPanel];
 #pragma unroll
       for (int k = 0; k < kQrPanel; ++k) w[k] = cmake<T>(0, 0);
-      for (int i = 0; i < mr; ++i) {
+      int i = 0;
+      for (; i + 4 <= mr; i += 4) {
+        cplx<T> q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = Q[static_cast<int64_t>(j0 + i + u) * steps + c];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int k = 0; k < kQrPanel; ++k)
+            if (k < jb) cfma(w[k], cconj(Vp[(i + u) * nb + k]), q[u]);
+      }
+      for (; i < mr; ++i) {
         const cplx<T> q = Q[static_cast<int64_t>(j0 + i) * steps + c];
 #pragma unroll
         for (int k = 0; k < kQrPanel; ++k)
@@ -601,20 +639,33 @@ __device__ void svd_onesided(int m, int n, cplx<T> *C, cplx<T> *V, T *sig2, int 
 // product.  With V, a w x w unitary Q accumulates the rotations of the visit
 // and is applied to V's matching columns afterwards, a chunk of V's rows at a
 // time through shared memory.  Outer sweeps repeat until one rotates nothing.
+// Sum over the 16 lanes of a half warp (mask: those lanes), the same value
+// broadcast to all of them.
+template <typename T>
+__device__ __forceinline__ T half_sum(T v, unsigned mask) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, 16);
+  return __shfl_sync(mask, v, 0, 16);
+}
+
+// One column pair (p, q) of a staged block, rotated by half a warp (the two
+// halves of a warp work on two disjoint pairs).
 template <typename T>
 __device__ void jacobi_rotate_staged(int m, int w, cplx<T> *Cb, cplx<T> *Q, T *nr, int p, int q, T tol,
                                      T negligible, int *flag) {
   const T al = nr[p], be = nr[q];
   if (!(al > negligible) || !(be > negligible)) return;
+  const int hl = lane_id() & 15;
+  const unsigned mask = 0xFFFFu << (lane_id() & 16);
   cplx<T> *cp = Cb + static_cast<int64_t>(p) * m, *cq = Cb + static_cast<int64_t>(q) * m;
   T gr = 0, gi = 0;
-  for (int i = lane_id(); i < m; i += 32) {
+  for (int i = hl; i < m; i += 16) {
     cplx<T> x = cp[i], y = cq[i];
     gr += x.re * y.re + x.im * y.im;  // conj(x) y
     gi += x.re * y.im - x.im * y.re;
   }
-  gr = __shfl_sync(0xffffffffu, warp_sum(gr), 0);
-  gi = __shfl_sync(0xffffffffu, warp_sum(gi), 0);
+  gr = half_sum(gr, mask);
+  gi = half_sum(gi, mask);
   const T absg = sqrt(gr * gr + gi * gi);
   if (!(absg > tol * sqrt(al) * sqrt(be))) return;
   const T zeta = (be - al) / (T(2) * absg);
@@ -624,7 +675,7 @@ __device__ void jacobi_rotate_staged(int m, int w, cplx<T> *Cb, cplx<T> *Q, T *n
   const T cs = T(1) / sqrt(T(1) + t * t), sn = t * cs;
   const cplx<T> uc = cmake<T>(gr / absg, -gi / absg);  // conj(gamma / |gamma|)
   T np = 0, nq = 0;
-  for (int i = lane_id(); i < m; i += 32) {
+  for (int i = hl; i < m; i += 16) {
     cplx<T> x = cp[i], y = cmul(uc, cq[i]);
     cplx<T> xn = cmake<T>(cs * x.re - sn * y.re, cs * x.im - sn * y.im);
     cplx<T> yn = cmake<T>(sn * x.re + cs * y.re, sn * x.im + cs * y.im);
@@ -633,18 +684,18 @@ __device__ void jacobi_rotate_staged(int m, int w, cplx<T> *Cb, cplx<T> *Q, T *n
     np += cabs2(xn);
     nq += cabs2(yn);
   }
-  np = __shfl_sync(0xffffffffu, warp_sum(np), 0);
-  nq = __shfl_sync(0xffffffffu, warp_sum(nq), 0);
+  np = half_sum(np, mask);
+  nq = half_sum(nq, mask);
   if (Q != nullptr) {
     cplx<T> *qp = Q + static_cast<int64_t>(p) * w, *qq = Q + static_cast<int64_t>(q) * w;
-    for (int i = lane_id(); i < w; i += 32) {
+    for (int i = hl; i < w; i += 16) {
       cplx<T> x = qp[i], y = cmul(uc, qq[i]);
       qp[i] = cmake<T>(cs * x.re - sn * y.re, cs * x.im - sn * y.im);
       qq[i] = cmake<T>(sn * x.re + cs * y.re, sn * x.im + cs * y.im);
     }
   }
-  __syncwarp();
-  if (lane_id() == 0) {
+  __syncwarp(mask);
+  if (hl == 0) {
     nr[p] = np;
     nr[q] = nq;
     *flag = 1;
@@ -661,7 +712,7 @@ __device__ void svd_onesided_blocked(int m, int n, cplx<T> *C, cplx<T> *V, T *si
   const bool withV = V != nullptr;
   int bw = 32;
   while (bw > 1 && static_cast<int64_t>(m) * 2 * bw + (withV ? 4 * bw * bw : 0) + 2 * bw > sbuf_elems) --bw;
-  if (bw > kWarps) bw -= bw % kWarps;  // whole waves of warps per step
+  if (bw > 2 * kWarps) bw -= bw % (2 * kWarps);  // whole waves of half warps per step
   const int nb = (n + bw - 1) / bw, nbe = nb + (nb & 1);
   const int max_sweeps = sizeof(T) == 4 ? kMaxBlockedSweepsF : kMaxBlockedSweepsD;
   int *any = flag + 1;
@@ -692,8 +743,9 @@ __device__ void svd_onesided_blocked(int m, int n, cplx<T> *C, cplx<T> *V, T *si
     __syncthreads();
     if (self) {
       const int mm = w + (w & 1), half = mm / 2;
+      const int hw = 2 * warp_id() + (lane_id() >> 4);  // half-warp index
       for (int round = 0; round < mm - 1; ++round) {
-        for (int pi = warp_id(); pi < half; pi += kWarps) {
+        for (int pi = hw; pi < half; pi += 2 * kWarps) {
           int p, q;
           if (pi == 0) { p = mm - 1; q = round; }
           else { p = (round + pi) % (mm - 1); q = (round - pi + (mm - 1)) % (mm - 1); }
@@ -706,8 +758,9 @@ __device__ void svd_onesided_blocked(int m, int n, cplx<T> *C, cplx<T> *V, T *si
     } else {
       const bool i_larger = wI >= wJ;
       const int wa = i_larger ? wI : wJ, wb = i_larger ? wJ : wI;
+      const int hw = 2 * warp_id() + (lane_id() >> 4);  // half-warp index
       for (int t = 0; t < wa; ++t) {
-        for (int b = warp_id(); b < wb; b += kWarps) {
+        for (int b = hw; b < wb; b += 2 * kWarps) {
           const int a = (b + t) % wa;
           const int p = i_larger ? a : b, q = wI + (i_larger ? b : a);
           jacobi_rotate_staged<T>(m, w, Cb, Q, nr, p, q, tol, negligible, flag);
