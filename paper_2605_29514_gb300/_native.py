@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libstn.so")
-SOURCES = ["engine.cu", "program.cpp", "api.cpp"]
+SOURCES = ["engine_f32.cu", "engine_f64.cu", "engine.cu", "engine_noalloc.cu", "program.cpp", "api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
@@ -32,7 +32,7 @@ def _compile(src):
 def build(force=False):
     """Compile the CUDA sources for sm_103a and link libstn.so in the package."""
     srcs = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(INCLUDE, "stn.h")]
-    srcs += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    srcs += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     if not force and os.path.exists(LIB):
         newest = max(os.path.getmtime(s) for s in srcs)
         if os.path.getmtime(LIB) >= newest:

@@ -1,132 +1,12 @@
-// Kernels of the stabilizer-tensor-network simulation (sm_103a).
-//
-// One persistent CTA per shot slot walks the op list of a program segment
-// (one syndrome round).  Clifford gates and Pauli noise update the inverse
-// tableau held in shared memory (bit-exact integer row operations, Sec. IV A).
-// A crosstalk rotation or a measurement pushes its Pauli through the tableau
-// and acts on the shot's MPS as a bond-2 Pauli-string MPO; the touched span
-// is then recompressed (Sec. IV B, Eq. 8) by a two-pass sweep:
-//   left sweep   R_{k+1} = R factor of (R_k A'_k), R_a = identity since the
-//                sites left of the span are left-canonical (Householder QR,
-//                no Q formed); ||R_b A'_b||^2 is the squared norm of the new
-//                state, which for a projector is the Born probability;
-//   right sweep  C = R_k M_k = U Sigma V^dag (one-sided Jacobi); the kept
-//                columns of V give the new right-canonical site and
-//                M_{k-1} = A'_{k-1} (M_k V_keep) carries the rest to the left.
-// Sigma holds the Schmidt values of the bond, so keeping the largest ones is
-// the truncation of Eq. 8.  Small bonds are decomposed in shared memory (in
-// double precision on the complex64 path where that fits); large bonds take
-// the Householder R factor of C and run Jacobi on its conjugate transpose,
-// which converges in a few sweeps.  Dense work runs in complex T (float or
-// double); norms, Born probabilities and log-probabilities in double.
-#include <cuda_runtime.h>
-#include <math.h>
-
-#include <mutex>
-
-#include "../../include/stn.h"
-#include "engine.h"
+// Host side of the simulation kernels: launch dispatch by precision, scratch
+// planning, and the small kernels (Philox uniforms, detectors).  The round,
+// init and dense-check kernels are instantiated in engine_f32.cu and
+// engine_f64.cu; the allocation-free SVD lives in engine_noalloc.cu.
+#include "engine_kernels.cuh"
 
 namespace stn {
 
-// ---------------------------------------------------------------------------
-// complex arithmetic
-template <typename T>
-struct cplx {
-  T re, im;
-};
-template <typename T>
-__device__ __forceinline__ cplx<T> cmake(T r, T i) {
-  cplx<T> c;
-  c.re = r;
-  c.im = i;
-  return c;
-}
-template <typename T>
-__device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) {
-  return cmake<T>(a.re + b.re, a.im + b.im);
-}
-template <typename T>
-__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
-  return cmake<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
-}
-template <typename T>
-__device__ __forceinline__ cplx<T> cconj(cplx<T> a) {
-  return cmake<T>(a.re, -a.im);
-}
-template <typename T>
-__device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) {
-  return cmake<T>(a.re * s, a.im * s);
-}
-// acc += a * b
-template <typename T>
-__device__ __forceinline__ void cfma(cplx<T> &acc, cplx<T> a, cplx<T> b) {
-  acc.re = fma(a.re, b.re, acc.re);
-  acc.re = fma(-a.im, b.im, acc.re);
-  acc.im = fma(a.re, b.im, acc.im);
-  acc.im = fma(a.im, b.re, acc.im);
-}
-template <typename T>
-__device__ __forceinline__ T cabs2(cplx<T> a) {
-  return a.re * a.re + a.im * a.im;
-}
-// i^m
-template <typename T>
-__device__ __forceinline__ cplx<T> ipow(int m) {
-  m &= 3;
-  return m == 0 ? cmake<T>(1, 0) : m == 1 ? cmake<T>(0, 1) : m == 2 ? cmake<T>(-1, 0) : cmake<T>(0, -1);
-}
-
-template <typename T>
-struct Eps;
-template <>
-struct Eps<float> {
-  static constexpr float v = 5.96e-8f;
-};
-template <>
-struct Eps<double> {
-  static constexpr double v = 1.11e-16;
-};
-
-// Complex elements of shared memory for the one-sided Jacobi SVD (the matrix
-// and its right singular vectors); larger problems run on global scratch.
-template <typename T>
-struct SvdSmem;
-template <>
-struct SvdSmem<float> {
-  static constexpr int elems = 22528;
-};
-template <>
-struct SvdSmem<double> {
-  static constexpr int elems = 8192;
-};
-constexpr int kMaxVec = 1024;  // longest Householder vector (4 * largest bond)
-
-constexpr int kBM = 64, kBN = 64, kBK = 16, kPad = 4;
-
-// ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): two 32x32->64-bit
-// multiplies per round, Weyl key schedule, ten rounds.
-__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t shot, uint32_t ev) {
-  uint32_t c0 = static_cast<uint32_t>(shot), c1 = static_cast<uint32_t>(shot >> 32);
-  uint32_t c2 = ev, c3 = 0u;
-  uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-    uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-    c0 = n0;
-    c1 = lo1;
-    c2 = n2;
-    c3 = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-  uint64_t bits = (static_cast<uint64_t>(c0) << 21) ^ static_cast<uint64_t>(c1 >> 11);
-  return static_cast<double>(bits) * 0x1.0p-53;
-}
-
+// Philox uniforms for tests: out[s][e] = u(seed, shot_offset + s, event_offset + e).
 __global__ void philox_kernel(uint64_t seed, uint64_t shot_offset, int64_t n_shots,
                               uint32_t event_offset, int n_events, double *out) {
   int64_t total = n_shots * static_cast<int64_t>(n_events);
@@ -136,1868 +16,6 @@ __global__ void philox_kernel(uint64_t seed, uint64_t shot_offset, int64_t n_sho
     uint32_t e = static_cast<uint32_t>(i % n_events);
     out[i] = philox_uniform(seed, shot_offset + static_cast<uint64_t>(s), event_offset + e);
   }
-}
-
-// ---------------------------------------------------------------------------
-// CTA-wide helpers
-__device__ __forceinline__ int tid() { return threadIdx.x; }
-
-// Sum of one double per thread over the CTA (red: kThreads doubles of smem).
-__device__ double block_sum(double v, double *red) {
-  red[tid()] = v;
-  __syncthreads();
-  for (int s = kThreads / 2; s > 0; s >>= 1) {
-    if (tid() < s) red[tid()] += red[tid() + s];
-    __syncthreads();
-  }
-  double r = red[0];
-  __syncthreads();
-  return r;
-}
-
-// C = alpha * op(A) op(B) + beta * C, all row-major, op = identity (0) or
-// conjugate transpose (1).  op(A) is M x K, op(B) is K x N.
-template <typename T, int TA, int TB>
-__device__ void cgemm(int M, int N, int K, cplx<T> alpha, const cplx<T> *A, int lda,
-                      const cplx<T> *B, int ldb, cplx<T> beta, cplx<T> *C, int ldc,
-                      cplx<T> *tile) {
-  cplx<T> *As = tile;                    // [kBK][kBM + kPad]
-  cplx<T> *Bs = tile + kBK * (kBM + kPad);  // [kBK][kBN + kPad]
-  const int ty = tid() / 16, tx = tid() % 16;
-  const int tilesM = (M + kBM - 1) / kBM, tilesN = (N + kBN - 1) / kBN;
-  for (int t = 0; t < tilesM * tilesN; ++t) {
-    const int i0 = (t / tilesN) * kBM, j0 = (t % tilesN) * kBN;
-    cplx<T> acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = cmake<T>(0, 0);
-    for (int k0 = 0; k0 < K; k0 += kBK) {
-      // A tile: element (i, k) of op(A)
-#pragma unroll
-      for (int r = 0; r < (kBM * kBK) / kThreads; ++r) {
-        int e = tid() + r * kThreads;
-        int i, k;
-        if (TA == 0) { k = e % kBK; i = e / kBK; } else { i = e % kBM; k = e / kBM; }
-        int gi = i0 + i, gk = k0 + k;
-        cplx<T> v = cmake<T>(0, 0);
-        if (gi < M && gk < K) v = TA == 0 ? A[static_cast<int64_t>(gi) * lda + gk]
-                                          : cconj(A[static_cast<int64_t>(gk) * lda + gi]);
-        As[k * (kBM + kPad) + i] = v;
-      }
-#pragma unroll
-      for (int r = 0; r < (kBN * kBK) / kThreads; ++r) {
-        int e = tid() + r * kThreads;
-        int j, k;
-        if (TB == 0) { j = e % kBN; k = e / kBN; } else { k = e % kBK; j = e / kBK; }
-        int gj = j0 + j, gk = k0 + k;
-        cplx<T> v = cmake<T>(0, 0);
-        if (gj < N && gk < K) v = TB == 0 ? B[static_cast<int64_t>(gk) * ldb + gj]
-                                          : cconj(B[static_cast<int64_t>(gj) * ldb + gk]);
-        Bs[k * (kBN + kPad) + j] = v;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int k = 0; k < kBK; ++k) {
-        cplx<T> av[4], bv[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = As[k * (kBM + kPad) + ty + 16 * a];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = Bs[k * (kBN + kPad) + tx + 16 * b];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) cfma(acc[a][b], av[a], bv[b]);
-      }
-      __syncthreads();
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      int gi = i0 + ty + 16 * a;
-      if (gi >= M) continue;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        int gj = j0 + tx + 16 * b;
-        if (gj >= N) continue;
-        cplx<T> *c = &C[static_cast<int64_t>(gi) * ldc + gj];
-        cplx<T> v = cmul(alpha, acc[a][b]);
-        if (beta.re != T(0) || beta.im != T(0)) v = cadd(v, cmul(beta, *c));
-        *c = v;
-      }
-    }
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
-__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
-constexpr int kWarps = kThreads / 32;
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Householder QR of B (m x n, row-major, leading dimension ld), in place: on
-// return rows 0..min(m,n)-1 hold R (upper trapezoidal) and the rest is zero.
-// Each step uses the Hermitian reflector P = I - 2 u u^dag with
-// P x = gamma e_1, gamma = -(x_0/|x_0|) ||x||.  Blocked by panels of nb
-// columns: a panel is copied to shared memory (pbuf) and factored there,
-// its reflectors u_1..u_nb are kept as the columns of V, and the product
-// P_nb ... P_1 = I - V T^dag V^dag (compact WY form, T upper triangular with
-// T_kk = 2, T[0:k, k] = -2 T[0:k, 0:k] V[:, 0:k]^dag u_k) is applied to the
-// trailing columns at once, one thread per column, so the trailing matrix is
-// read and written twice per panel rather than per column.  pbuf needs
-// m nb + 2 nb^2 complex elements (nb is reduced to fit).  CTA-wide.
-constexpr int kQrPanel = 16;
-
-__device__ __forceinline__ int qr_panel_width(int m, int pbuf_elems) {
-  int nb = kQrPanel;
-  while (nb > 1 && static_cast<int64_t>(m) * nb + 2 * nb * nb > pbuf_elems) --nb;
-  return nb;
-}
-
-// T of the compact WY form of a panel's reflectors (columns of Vp, row-major
-// [mr][nb], u_b zero above row b): T upper triangular, T_kk = 2,
-// T[0:k, k] = -2 T[0:k, 0:k] (V[:, 0:k]^dag u_k).  G is scratch.  CTA-wide.
-template <typename T>
-__device__ void wy_t_factor(int mr, int jb, int nb, const cplx<T> *Vp, cplx<T> *Tm, cplx<T> *G) {
-  for (int pr = warp_id(); pr < jb * jb; pr += kWarps) {
-    const int a = pr / jb, b = pr % jb;
-    if (a >= b) continue;
-    T gr = 0, gi = 0;
-    for (int i = b + lane_id(); i < mr; i += 32) {  // u_b vanishes above row b
-      const cplx<T> x = Vp[i * nb + a], y = Vp[i * nb + b];
-      gr += x.re * y.re + x.im * y.im;
-      gi += x.re * y.im - x.im * y.re;
-    }
-    gr = warp_sum(gr);
-    gi = warp_sum(gi);
-    if (lane_id() == 0) G[a * nb + b] = cmake<T>(gr, gi);
-  }
-  __syncthreads();
-  if (tid() == 0) {
-    for (int k = 0; k < jb; ++k) {
-      Tm[k * nb + k] = cmake<T>(2, 0);
-      for (int a = 0; a < k; ++a) {
-        cplx<T> acc = cmake<T>(0, 0);
-        for (int b = a; b < k; ++b) cfma(acc, Tm[a * nb + b], G[b * nb + k]);
-        Tm[a * nb + k] = cscale(acc, T(-2));
-      }
-    }
-  }
-  __syncthreads();
-}
-
-// With vstore (row-major m x min(m,n)), the reflectors are also kept there
-// (column j holds u_j in rows j..m-1; rows above are not written) so that
-// form_q can build Q explicitly.
-template <typename T>
-__device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *pbuf, int pbuf_elems, double *red,
-                             double *dm, cplx<T> *vstore = nullptr) {
-  const int steps = min(m, n);
-  const int nb = qr_panel_width(m, pbuf_elems);
-  cplx<T> *Vp = pbuf;                                   // [(m - j0)][nb], row-major
-  cplx<T> *Tm = pbuf + static_cast<int64_t>(m) * nb;  // [nb][nb]
-  cplx<T> *G = Tm + nb * nb;                            // [nb][nb], G[a][b] = u_a^dag u_b
-  for (int j0 = 0; j0 < steps; j0 += nb) {
-    const int jb = min(nb, steps - j0);
-    const int mr = m - j0;
-    for (int e = tid(); e < mr * jb; e += kThreads) {
-      const int i = e / jb, c = e % jb;
-      Vp[i * nb + c] = B[static_cast<int64_t>(j0 + i) * ld + j0 + c];
-    }
-    __syncthreads();
-    for (int jj = 0; jj < jb; ++jj) {
-      double nx2 = 0;
-      for (int i = jj + tid(); i < mr; i += kThreads) nx2 += static_cast<double>(cabs2(Vp[i * nb + jj]));
-      nx2 = block_sum(nx2, red);
-      // rows above the diagonal of this column are final R entries
-      for (int i = tid(); i < jj; i += kThreads) B[static_cast<int64_t>(j0 + i) * ld + j0 + jj] = Vp[i * nb + jj];
-      if (!(nx2 > 0.0)) {  // zero column: no reflector, R row jj is final
-        for (int i = tid(); i < mr; i += kThreads) {
-          if (i >= jj) B[static_cast<int64_t>(j0 + i) * ld + j0 + jj] = cmake<T>(0, 0);
-          Vp[i * nb + jj] = cmake<T>(0, 0);
-        }
-        __syncthreads();
-        continue;
-      }
-      if (tid() == 0) {
-        cplx<T> al = Vp[jj * nb + jj];
-        double aa = sqrt(static_cast<double>(cabs2(al)));
-        double nx = sqrt(nx2);
-        double pr = aa > 0 ? al.re / aa : 1.0, pi = aa > 0 ? al.im / aa : 0.0;
-        dm[0] = -pr * nx;  // gamma
-        dm[1] = -pi * nx;
-        dm[2] = 1.0 / sqrt(2.0 * nx * (nx + aa));  // 1 / ||x - gamma e_1||
-      }
-      __syncthreads();
-      const cplx<T> gam = cmake<T>(static_cast<T>(dm[0]), static_cast<T>(dm[1]));
-      const T sc = static_cast<T>(dm[2]);
-      for (int i = tid(); i < mr; i += kThreads) {
-        cplx<T> u = cmake<T>(0, 0);
-        if (i >= jj) {
-          cplx<T> x = Vp[i * nb + jj];
-          if (i == jj) x = cmake<T>(x.re - gam.re, x.im - gam.im);
-          u = cscale(x, sc);
-          B[static_cast<int64_t>(j0 + i) * ld + j0 + jj] = i == jj ? gam : cmake<T>(0, 0);
-        }
-        Vp[i * nb + jj] = u;
-      }
-      __syncthreads();
-      // the rest of the panel: b <- b - 2 u (u^dag b), one warp per column
-      for (int c = jj + 1 + warp_id(); c < jb; c += kWarps) {
-        T sr = 0, si = 0;
-        for (int i = jj + lane_id(); i < mr; i += 32) {
-          const cplx<T> u = Vp[i * nb + jj], b = Vp[i * nb + c];
-          sr += u.re * b.re + u.im * b.im;
-          si += u.re * b.im - u.im * b.re;
-        }
-        sr = __shfl_sync(0xffffffffu, warp_sum(sr), 0);
-        si = __shfl_sync(0xffffffffu, warp_sum(si), 0);
-        const cplx<T> s2 = cmake<T>(T(2) * sr, T(2) * si);
-        for (int i = jj + lane_id(); i < mr; i += 32) {
-          const cplx<T> t = cmul(Vp[i * nb + jj], s2);
-          cplx<T> &b = Vp[i * nb + c];
-          b = cmake<T>(b.re - t.re, b.im - t.im);
-        }
-      }
-      __syncthreads();
-    }
-    if (vstore != nullptr)
-      for (int e = tid(); e < mr * jb; e += kThreads) {
-        const int i = e / jb, c = e % jb;
-        vstore[static_cast<int64_t>(j0 + i) * steps + j0 + c] = Vp[i * nb + c];
-      }
-    if (j0 + jb >= n) {  // no trailing columns
-      __syncthreads();
-      continue;
-    }
-    wy_t_factor<T>(mr, jb, nb, Vp, Tm, G);
-    // trailing columns: b <- b - V (T^dag (V^dag b)); rows go four at a
-    // time so that four loads per thread are in flight
-    for (int c = j0 + jb + tid(); c < n; c += kThreads) {
-      cplx<T> w[kQrPanel];
-#pragma unroll
-      for (int k = 0; k < kQrPanel; ++k) w[k] = cmake<T>(0, 0);
-      int i = 0;
-      for (; i + 4 <= mr; i += 4) {
-        cplx<T> b[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) b[u] = B[static_cast<int64_t>(j0 + i + u) * ld + c];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int k = 0; k < kQrPanel; ++k)
-            if (k < jb) cfma(w[k], cconj(Vp[(i + u) * nb + k]), b[u]);
-      }
-      for (; i < mr; ++i) {
-        const cplx<T> b = B[static_cast<int64_t>(j0 + i) * ld + c];
-#pragma unroll
-        for (int k = 0; k < kQrPanel; ++k)
-          if (k < jb) cfma(w[k], cconj(Vp[i * nb + k]), b);
-      }
-      // w <- T^dag w in place, highest index first: w'[a] = sum_{b<=a} conj(T[b][a]) w[b]
-#pragma unroll
-      for (int a = kQrPanel - 1; a >= 0; --a) {
-        if (a >= jb) continue;
-        cplx<T> acc = cmake<T>(0, 0);
-#pragma unroll
-        for (int b = 0; b <= a; ++b) cfma(acc, cconj(Tm[b * nb + a]), w[b]);
-        w[a] = acc;
-      }
-      for (i = 0; i + 4 <= mr; i += 4) {
-        cplx<T> b[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) b[u] = B[static_cast<int64_t>(j0 + i + u) * ld + c];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-#pragma unroll
-          for (int k = 0; k < kQrPanel; ++k)
-            if (k < jb) {
-              const cplx<T> t = cmul(Vp[(i + u) * nb + k], w[k]);
-              b[u] = cmake<T>(b[u].re - t.re, b[u].im - t.im);
-            }
-          B[static_cast<int64_t>(j0 + i + u) * ld + c] = b[u];
-        }
-      }
-      for (; i < mr; ++i) {
-        cplx<T> &bref = B[static_cast<int64_t>(j0 + i) * ld + c];
-        cplx<T> acc = bref;
-#pragma unroll
-        for (int k = 0; k < kQrPanel; ++k)
-          if (k < jb) {
-            const cplx<T> t = cmul(Vp[i * nb + k], w[k]);
-            acc = cmake<T>(acc.re - t.re, acc.im - t.im);
-          }
-        bref = acc;
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Explicit Q (m x steps, row-major) of a Householder QR whose reflectors
-// qr_r_inplace kept in vstore: Q = P_1 ... P_steps [I; 0], built panel by
-// panel from the last, each panel applied as I - V T V^dag to the columns at
-// or right of it (the columns left of panel p are unit vectors its
-// reflectors do not touch).  Same shared-memory needs as qr_r_inplace.
-template <typename T>
-__device__ void form_q(int m, int steps, const cplx<T> *vstore, cplx<T> *Q, cplx<T> *pbuf, int pbuf_elems) {
-  const int nb = qr_panel_width(m, pbuf_elems);
-  cplx<T> *Vp = pbuf;
-  cplx<T> *Tm = pbuf + static_cast<int64_t>(m) * nb;
-  cplx<T> *G = Tm + nb * nb;
-  for (int64_t e = tid(); e < static_cast<int64_t>(m) * steps; e += kThreads) {
-    const int i = static_cast<int>(e / steps), c = static_cast<int>(e % steps);
-    Q[e] = cmake<T>(i == c ? T(1) : T(0), 0);
-  }
-  const int npan = (steps + nb - 1) / nb;
-  for (int p = npan - 1; p >= 0; --p) {
-    const int j0 = p * nb, jb = min(nb, steps - j0), mr = m - j0;
-    for (int e = tid(); e < mr * nb; e += kThreads) {
-      const int i = e / nb, c = e % nb;
-      // u_c is zero above its own row; rows above were never written
-      Vp[e] = (c < jb && i >= c) ? vstore[static_cast<int64_t>(j0 + i) * steps + j0 + c] : cmake<T>(0, 0);
-    }
-    __syncthreads();
-    wy_t_factor<T>(mr, jb, nb, Vp, Tm, G);
-    for (int c = j0 + tid(); c < steps; c += kThreads) {
-      cplx<T> w[kQrPanel];
-#pragma unroll
-      for (int k = 0; k < kQrPanel; ++k) w[k] = cmake<T>(0, 0);
-      int i = 0;
-      for (; i + 4 <= mr; i += 4) {
-        cplx<T> q[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) q[u] = Q[static_cast<int64_t>(j0 + i + u) * steps + c];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int k = 0; k < kQrPanel; ++k)
-            if (k < jb) cfma(w[k], cconj(Vp[(i + u) * nb + k]), q[u]);
-      }
-      for (; i < mr; ++i) {
-        const cplx<T> q = Q[static_cast<int64_t>(j0 + i) * steps + c];
-#pragma unroll
-        for (int k = 0; k < kQrPanel; ++k)
-          if (k < jb) cfma(w[k], cconj(Vp[i * nb + k]), q);
-      }
-      // w <- T w in place, lowest index first: w'[a] = sum_{b>=a} T[a][b] w[b]
-#pragma unroll
-      for (int a = 0; a < kQrPanel; ++a) {
-        if (a >= jb) continue;
-        cplx<T> acc = cmake<T>(0, 0);
-#pragma unroll
-        for (int b = a; b < kQrPanel; ++b)
-          if (b < jb) cfma(acc, Tm[a * nb + b], w[b]);
-        w[a] = acc;
-      }
-      for (int i = 0; i < mr; ++i) {
-        cplx<T> &qref = Q[static_cast<int64_t>(j0 + i) * steps + c];
-        cplx<T> acc = qref;
-#pragma unroll
-        for (int k = 0; k < kQrPanel; ++k)
-          if (k < jb) {
-            const cplx<T> t = cmul(Vp[i * nb + k], w[k]);
-            acc = cmake<T>(acc.re - t.re, acc.im - t.im);
-          }
-        qref = acc;
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// One-sided (Hestenes) Jacobi SVD.  Columns of C (m x n, column-major,
-// leading dimension m) are rotated pairwise until mutually orthogonal, so
-// that C V = U diag(sigma); V (column-major) accumulates the rotations unless
-// it is null (then only the rotated columns, U diag(sigma), are wanted).
-// Round-robin ordering, one warp per column pair, the pairs of a round are
-// disjoint.  A pair is left alone when its columns are orthogonal to the
-// rounding level of their dot products, or when one column is negligible
-// (norm at the rounding level of ||C||: no information, and its dot products
-// would underflow).
-
-// One sweep over all column pairs of C (ldc = m) with V (n x n, ld = ldv).
-// Sets *flag when a rotation happened.  CTA-wide.
-template <typename T>
-__device__ void onesided_sweep(int m, int n, cplx<T> *C, cplx<T> *V, int ldv, T tol, T negligible,
-                               int *flag) {
-  const int mm = n + (n & 1);
-  const int half = mm / 2;
-  for (int round = 0; round < mm - 1; ++round) {
-    for (int pi = warp_id(); pi < half; pi += kWarps) {
-      int p, q;
-      if (pi == 0) { p = mm - 1; q = round; }
-      else { p = (round + pi) % (mm - 1); q = (round - pi + (mm - 1)) % (mm - 1); }
-      if (p > q) { int t = p; p = q; q = t; }
-      if (q >= n) continue;
-      cplx<T> *cp = C + static_cast<int64_t>(p) * m, *cq = C + static_cast<int64_t>(q) * m;
-      T al = 0, be = 0, gr = 0, gi = 0;
-      for (int i = lane_id(); i < m; i += 32) {
-        cplx<T> x = cp[i], y = cq[i];
-        al += cabs2(x);
-        be += cabs2(y);
-        gr += x.re * y.re + x.im * y.im;  // conj(x) y
-        gi += x.re * y.im - x.im * y.re;
-      }
-      al = __shfl_sync(0xffffffffu, warp_sum(al), 0);
-      be = __shfl_sync(0xffffffffu, warp_sum(be), 0);
-      gr = __shfl_sync(0xffffffffu, warp_sum(gr), 0);
-      gi = __shfl_sync(0xffffffffu, warp_sum(gi), 0);
-      if (!(al > negligible) || !(be > negligible)) continue;
-      T absg = sqrt(gr * gr + gi * gi);
-      if (!(absg > tol * sqrt(al) * sqrt(be))) continue;
-      T zeta = (be - al) / (T(2) * absg);
-      T az = fabs(zeta);
-      T t = az > T(1e10) ? T(0.5) / az : T(1) / (az + sqrt(T(1) + zeta * zeta));
-      if (zeta < 0) t = -t;
-      T cs = T(1) / sqrt(T(1) + t * t), sn = t * cs;
-      cplx<T> uc = cmake<T>(gr / absg, -gi / absg);  // conj(gamma / |gamma|)
-      for (int i = lane_id(); i < m; i += 32) {
-        cplx<T> x = cp[i], y = cmul(uc, cq[i]);
-        cp[i] = cmake<T>(cs * x.re - sn * y.re, cs * x.im - sn * y.im);
-        cq[i] = cmake<T>(sn * x.re + cs * y.re, sn * x.im + cs * y.im);
-      }
-      if (V == nullptr) {
-        if (lane_id() == 0) *flag = 1;
-        continue;
-      }
-      cplx<T> *vp = V + static_cast<int64_t>(p) * ldv, *vq = V + static_cast<int64_t>(q) * ldv;
-      for (int i = lane_id(); i < n; i += 32) {
-        cplx<T> x = vp[i], y = cmul(uc, vq[i]);
-        vp[i] = cmake<T>(cs * x.re - sn * y.re, cs * x.im - sn * y.im);
-        vq[i] = cmake<T>(sn * x.re + cs * y.re, sn * x.im + cs * y.im);
-      }
-      if (lane_id() == 0) *flag = 1;
-    }
-    __syncthreads();
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ T onesided_tol(int m) {
-  return Eps<T>::v * T(4) * sqrt(static_cast<T>(m > 1 ? m : 1));
-}
-
-template <typename T>
-__device__ T onesided_prologue(int m, int n, const cplx<T> *C, cplx<T> *V, double *red) {
-  for (int e = tid(); V != nullptr && e < n * n; e += kThreads) {
-    int j = e / n, i = e % n;
-    V[e] = cmake<T>(i == j ? T(1) : T(0), 0);
-  }
-  double fro2 = 0;
-  for (int64_t e = tid(); e < static_cast<int64_t>(m) * n; e += kThreads) fro2 += static_cast<double>(cabs2(C[e]));
-  fro2 = block_sum(fro2, red);
-  return static_cast<T>(static_cast<double>(Eps<T>::v) * static_cast<double>(Eps<T>::v) * fro2);
-}
-
-template <typename T>
-__device__ void onesided_epilogue(int m, int n, const cplx<T> *C, T *sig2) {
-  for (int j = warp_id(); j < n; j += kWarps) {
-    double a = 0;
-    for (int i = lane_id(); i < m; i += 32) a += static_cast<double>(cabs2(C[static_cast<int64_t>(j) * m + i]));
-    a = warp_sum(a);
-    if (lane_id() == 0) sig2[j] = static_cast<T>(a);
-  }
-  __syncthreads();
-}
-
-constexpr int kMaxSweepsF = 15, kMaxSweepsD = 20;
-constexpr int kMaxBlockedSweepsF = 30, kMaxBlockedSweepsD = 40;
-
-// Unblocked: C and V wherever they are (shared memory for small problems).
-template <typename T>
-__device__ void svd_onesided(int m, int n, cplx<T> *C, cplx<T> *V, T *sig2, int *flag, double *red) {
-  const T negligible = onesided_prologue<T>(m, n, C, V, red);
-  const T tol = onesided_tol<T>(m);
-  const int max_sweeps = sizeof(T) == 4 ? kMaxSweepsF : kMaxSweepsD;
-  for (int sweep = 0; sweep < max_sweeps && n > 1; ++sweep) {
-    if (tid() == 0) *flag = 0;
-    __syncthreads();
-    onesided_sweep<T>(m, n, C, V, n, tol, negligible, flag);
-    int f = *flag;
-    __syncthreads();
-    if (!f) break;
-  }
-  onesided_epilogue<T>(m, n, C, sig2);
-}
-
-// Blocked, for problems larger than shared memory: C (m x n, column-major)
-// and V (n x n, or null) stay in global memory and the columns are split into
-// blocks of bw.  One outer sweep first orthogonalises the columns inside every
-// block, then lets every pair of blocks exchange its cross pairs: the block
-// pairs of a tournament round are disjoint, and inside a block pair (I, J)
-// step t rotates the disjoint column pairs (b, (b + t) mod w_a) over the
-// smaller block's columns b and the larger block's columns, so each cross
-// pair is visited once per sweep.  A visited block (or block pair) is staged
-// in shared memory with its squared column norms, which the warp that rotates
-// a pair recomputes from the rotated columns, so testing a pair costs one dot
-// product.  With V, a w x w unitary Q accumulates the rotations of the visit
-// and is applied to V's matching columns afterwards, a chunk of V's rows at a
-// time through shared memory.  Outer sweeps repeat until one rotates nothing.
-// Sum over the 16 lanes of a half warp (mask: those lanes), the same value
-// broadcast to all of them.
-template <typename T>
-__device__ __forceinline__ T half_sum(T v, unsigned mask) {
-#pragma unroll
-  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, 16);
-  return __shfl_sync(mask, v, 0, 16);
-}
-
-// One column pair (p, q) of a staged block, rotated by half a warp (the two
-// halves of a warp work on two disjoint pairs).
-template <typename T>
-__device__ void jacobi_rotate_staged(int m, int w, cplx<T> *Cb, cplx<T> *Q, T *nr, int p, int q, T tol,
-                                     T negligible, int *flag) {
-  const T al = nr[p], be = nr[q];
-  if (!(al > negligible) || !(be > negligible)) return;
-  const int hl = lane_id() & 15;
-  const unsigned mask = 0xFFFFu << (lane_id() & 16);
-  cplx<T> *cp = Cb + static_cast<int64_t>(p) * m, *cq = Cb + static_cast<int64_t>(q) * m;
-  T gr = 0, gi = 0;
-  for (int i = hl; i < m; i += 16) {
-    cplx<T> x = cp[i], y = cq[i];
-    gr += x.re * y.re + x.im * y.im;  // conj(x) y
-    gi += x.re * y.im - x.im * y.re;
-  }
-  gr = half_sum(gr, mask);
-  gi = half_sum(gi, mask);
-  const T absg = sqrt(gr * gr + gi * gi);
-  if (!(absg > tol * sqrt(al) * sqrt(be))) return;
-  const T zeta = (be - al) / (T(2) * absg);
-  const T az = fabs(zeta);
-  T t = az > T(1e10) ? T(0.5) / az : T(1) / (az + sqrt(T(1) + zeta * zeta));
-  if (zeta < 0) t = -t;
-  const T cs = T(1) / sqrt(T(1) + t * t), sn = t * cs;
-  const cplx<T> uc = cmake<T>(gr / absg, -gi / absg);  // conj(gamma / |gamma|)
-  T np = 0, nq = 0;
-  for (int i = hl; i < m; i += 16) {
-    cplx<T> x = cp[i], y = cmul(uc, cq[i]);
-    cplx<T> xn = cmake<T>(cs * x.re - sn * y.re, cs * x.im - sn * y.im);
-    cplx<T> yn = cmake<T>(sn * x.re + cs * y.re, sn * x.im + cs * y.im);
-    cp[i] = xn;
-    cq[i] = yn;
-    np += cabs2(xn);
-    nq += cabs2(yn);
-  }
-  np = half_sum(np, mask);
-  nq = half_sum(nq, mask);
-  if (Q != nullptr) {
-    cplx<T> *qp = Q + static_cast<int64_t>(p) * w, *qq = Q + static_cast<int64_t>(q) * w;
-    for (int i = hl; i < w; i += 16) {
-      cplx<T> x = qp[i], y = cmul(uc, qq[i]);
-      qp[i] = cmake<T>(cs * x.re - sn * y.re, cs * x.im - sn * y.im);
-      qq[i] = cmake<T>(sn * x.re + cs * y.re, sn * x.im + cs * y.im);
-    }
-  }
-  __syncwarp(mask);
-  if (hl == 0) {
-    nr[p] = np;
-    nr[q] = nq;
-    *flag = 1;
-  }
-}
-
-template <typename T>
-__device__ void svd_onesided_blocked(int m, int n, cplx<T> *C, cplx<T> *V, T *sig2, int *flag,
-                                     double *red, cplx<T> *sbuf, int sbuf_elems) {
-  const T negligible = onesided_prologue<T>(m, n, C, V, red);
-  const T tol = onesided_tol<T>(m);
-  // staged block pair: Q (w x w, only with V), norms (w complex slots),
-  // columns (m x w)
-  const bool withV = V != nullptr;
-  int bw = 32;
-  while (bw > 1 && static_cast<int64_t>(m) * 2 * bw + (withV ? 4 * bw * bw : 0) + 2 * bw > sbuf_elems) --bw;
-  if (bw > 2 * kWarps) bw -= bw % (2 * kWarps);  // whole waves of half warps per step
-  const int nb = (n + bw - 1) / bw, nbe = nb + (nb & 1);
-  const int max_sweeps = sizeof(T) == 4 ? kMaxBlockedSweepsF : kMaxBlockedSweepsD;
-  int *any = flag + 1;
-
-  auto visit = [&](int I, int J) {
-    const bool self = I == J;
-    const int c0 = I * bw, wI = min(bw, n - c0);
-    const int c1 = J * bw, wJ = self ? 0 : min(bw, n - c1);
-    const int w = wI + wJ;
-    auto gcol = [&](int c) { return c < wI ? c0 + c : c1 + (c - wI); };
-    const int qe = withV ? w * w : 0;
-    cplx<T> *Q = withV ? sbuf : nullptr;
-    T *nr = reinterpret_cast<T *>(sbuf + qe);
-    cplx<T> *Cb = sbuf + qe + w;
-    for (int e = tid(); e < m * w; e += kThreads) {
-      const int c = e / m, i = e % m;
-      Cb[e] = C[static_cast<int64_t>(gcol(c)) * m + i];
-    }
-    for (int e = tid(); e < qe; e += kThreads) Q[e] = cmake<T>((e / w) == (e % w) ? T(1) : T(0), 0);
-    __syncthreads();
-    for (int c = warp_id(); c < w; c += kWarps) {
-      T a = 0;
-      for (int i = lane_id(); i < m; i += 32) a += cabs2(Cb[static_cast<int64_t>(c) * m + i]);
-      a = __shfl_sync(0xffffffffu, warp_sum(a), 0);
-      if (lane_id() == 0) nr[c] = a;
-    }
-    if (tid() == 0) *flag = 0;
-    __syncthreads();
-    if (self) {
-      const int mm = w + (w & 1), half = mm / 2;
-      const int hw = 2 * warp_id() + (lane_id() >> 4);  // half-warp index
-      for (int round = 0; round < mm - 1; ++round) {
-        for (int pi = hw; pi < half; pi += 2 * kWarps) {
-          int p, q;
-          if (pi == 0) { p = mm - 1; q = round; }
-          else { p = (round + pi) % (mm - 1); q = (round - pi + (mm - 1)) % (mm - 1); }
-          if (p > q) { int tt = p; p = q; q = tt; }
-          if (q >= w) continue;
-          jacobi_rotate_staged<T>(m, w, Cb, Q, nr, p, q, tol, negligible, flag);
-        }
-        __syncthreads();
-      }
-    } else {
-      const bool i_larger = wI >= wJ;
-      const int wa = i_larger ? wI : wJ, wb = i_larger ? wJ : wI;
-      const int hw = 2 * warp_id() + (lane_id() >> 4);  // half-warp index
-      for (int t = 0; t < wa; ++t) {
-        for (int b = hw; b < wb; b += 2 * kWarps) {
-          const int a = (b + t) % wa;
-          const int p = i_larger ? a : b, q = wI + (i_larger ? b : a);
-          jacobi_rotate_staged<T>(m, w, Cb, Q, nr, p, q, tol, negligible, flag);
-        }
-        __syncthreads();
-      }
-    }
-    const int rotated = *flag;
-    __syncthreads();
-    if (!rotated) return;
-    for (int e = tid(); e < m * w; e += kThreads) {
-      const int c = e / m, i = e % m;
-      C[static_cast<int64_t>(gcol(c)) * m + i] = Cb[e];
-    }
-    __syncthreads();
-    // V[:, cols] <- V[:, cols] Q, rows staged in the column buffer
-    const int rows_cap = (sbuf_elems - qe - w) / w;
-    for (int i0 = 0; withV && i0 < n; i0 += rows_cap) {
-      const int rows = min(rows_cap, n - i0);
-      for (int e = tid(); e < rows * w; e += kThreads) {
-        const int c = e / rows, i = e % rows;
-        Cb[e] = V[static_cast<int64_t>(gcol(c)) * n + i0 + i];
-      }
-      __syncthreads();
-      // four output columns per thread: one staged element feeds four FMAs
-      const int groups = (w + 3) / 4;
-      for (int e = tid(); e < rows * groups; e += kThreads) {
-        const int g = e / rows, i = e % rows, cb = 4 * g;
-        cplx<T> acc[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = cmake<T>(0, 0);
-        for (int j = 0; j < w; ++j) {
-          const cplx<T> v = Cb[j * rows + i];
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (cb + u < w) cfma(acc[u], v, Q[(cb + u) * w + j]);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (cb + u < w) V[static_cast<int64_t>(gcol(cb + u)) * n + i0 + i] = acc[u];
-      }
-      __syncthreads();
-    }
-    if (tid() == 0) *any = 1;
-  };
-
-  for (int sweep = 0; sweep < max_sweeps && n > 1; ++sweep) {
-    if (tid() == 0) *any = 0;
-    __syncthreads();
-    for (int I = 0; I < nb; ++I) visit(I, I);
-    for (int round = 0; round < nbe - 1; ++round) {
-      for (int bp = 0; bp < nbe / 2; ++bp) {
-        int I, J;
-        if (bp == 0) { I = nbe - 1; J = round; }
-        else { I = (round + bp) % (nbe - 1); J = (round - bp + (nbe - 1)) % (nbe - 1); }
-        if (I > J) { int tt = I; I = J; J = tt; }
-        if (J >= nb) continue;
-        visit(I, J);
-      }
-    }
-    __syncthreads();
-    const int f = *any;
-    __syncthreads();
-    if (!f) break;
-  }
-  onesided_epilogue<T>(m, n, C, sig2);
-}
-
-// One Newton-Schulz step X <- X (3 I - X^dag X) / 2 on the k orthonormal-to-
-// rounding columns of X (n x k, row-major, ld k): the accumulated rotations
-// leave X orthonormal only to about sqrt(#rotations) eps; this brings it back
-// to the rounding level of one product.  G and Y are k x k and n x k scratch.
-template <typename T>
-__device__ void reorthonormalize(int n, int k, cplx<T> *X, cplx<T> *G, cplx<T> *Y, cplx<T> *tile) {
-  const cplx<T> one = cmake<T>(1, 0), zero = cmake<T>(0, 0);
-  cgemm<T, 1, 0>(k, k, n, one, X, k, X, k, zero, G, k, tile);
-  for (int e = tid(); e < k * k; e += kThreads) {
-    int i = e / k, j = e % k;
-    cplx<T> g = G[e];
-    G[e] = cmake<T>((i == j ? T(1.5) : T(0)) - T(0.5) * g.re, -T(0.5) * g.im);
-  }
-  __syncthreads();
-  cgemm<T, 0, 0>(n, k, k, one, X, k, G, k, zero, Y, k, tile);
-  for (int e = tid(); e < n * k; e += kThreads) X[e] = Y[e];
-  __syncthreads();
-}
-
-// Descending order of lambda (ties by index): perm[rank] = index.
-template <typename T>
-__device__ void sort_desc(int n, const T *lam, int *perm) {
-  for (int i = tid(); i < n; i += kThreads) perm[i] = i;
-  __syncthreads();
-  for (int i = tid(); i < n; i += kThreads) {
-    T li = lam[i];
-    int rank = 0;
-    for (int j = 0; j < n; ++j) {
-      T lj = lam[j];
-      rank += (lj > li) || (lj == li && j < i);
-    }
-    if (li == li && rank < n) perm[rank] = i;  // a NaN keeps the identity slot
-  }
-  __syncthreads();
-}
-
-// ---------------------------------------------------------------------------
-// The MPO of one rotation or measurement.
-enum MpoKind { MPO_ROT = 0, MPO_PROJ_Z = 1, MPO_PROJ_B = 2 };
-
-template <typename T>
-struct MpoSpec {
-  int kind, lo, hi, j;
-  cplx<T> w0, w1;  // branch weights (folded into site lo)
-  cplx<T> v0, v1;  // measurement eigenvector at site j (case B)
-};
-
-// 2x2 operator (row-major op[s*2 + t]) of branch `br` at site k of the span.
-template <typename T>
-__device__ void site_op(const MpoSpec<T> &sp, const uint64_t *ppx, const uint64_t *ppz, int k,
-                        int br, cplx<T> op[4]) {
-  const bool x = (ppx[k >> 6] >> (k & 63)) & 1, z = (ppz[k >> 6] >> (k & 63)) & 1;
-  const cplx<T> zero = cmake<T>(0, 0), one = cmake<T>(1, 0);
-  op[0] = one; op[1] = zero; op[2] = zero; op[3] = one;
-  if (br == 1) {
-    if (sp.kind == MPO_PROJ_B && k == sp.j) {
-      op[0] = zero; op[1] = cconj(sp.v1); op[2] = zero; op[3] = zero;
-    } else if (sp.kind == MPO_PROJ_B) {
-      // Hermitian letter of P' at k (controlled-Pauli target)
-      if (x && !z) { op[0] = zero; op[1] = one; op[2] = one; op[3] = zero; }
-      else if (x && z) { op[0] = zero; op[1] = cmake<T>(0, -1); op[2] = cmake<T>(0, 1); op[3] = zero; }
-      else if (z) { op[3] = cmake<T>(-1, 0); }
-    } else {
-      // X^x Z^z (MPO_PROJ_Z has x = 0 on every site)
-      if (x && !z) { op[0] = zero; op[1] = one; op[2] = one; op[3] = zero; }
-      else if (x && z) { op[0] = zero; op[1] = cmake<T>(-1, 0); op[2] = one; op[3] = zero; }
-      else if (z) { op[3] = cmake<T>(-1, 0); }
-    }
-  } else if (sp.kind == MPO_PROJ_B && k == sp.j) {
-    op[0] = cconj(sp.v0); op[3] = zero;
-  }
-  if (k == sp.lo) {
-    cplx<T> w = br == 0 ? sp.w0 : sp.w1;
-    for (int i = 0; i < 4; ++i) op[i] = cmul(w, op[i]);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Shared-memory layout of the round kernel.
-template <typename T>
-struct Smem {
-  uint64_t *tx, *tz, *ppx, *ppz;
-  uint8_t *tm;
-  int *chi, *perm, *misc;
-  int64_t *off;  // span offsets: Ap stack [n+2], G stack [n+2]
-  int64_t *goff;
-  double *red;
-  double *dmisc;
-  cplx<T> *tile;
-  cplx<T> *jbuf, *uvec;
-  int *rdim;
-  T *lam;
-  MpoSpec<T> *spec;
-};
-
-template <typename T>
-__host__ __device__ size_t smem_bytes(int n, int W, int svd_elems) {
-  size_t b = 0;
-  auto add = [&](size_t bytes) { b += (bytes + 15) & ~size_t(15); };
-  add(sizeof(uint64_t) * 2 * n * W);  // tx
-  add(sizeof(uint64_t) * 2 * n * W);  // tz
-  add(sizeof(uint64_t) * W);          // ppx
-  add(sizeof(uint64_t) * W);          // ppz
-  add(2 * n);                         // tm
-  add(sizeof(int) * (n + 2));         // chi
-  add(sizeof(int) * 512);             // perm
-  add(sizeof(int) * 16);              // misc
-  add(sizeof(int64_t) * (n + 2));     // off
-  add(sizeof(int64_t) * (n + 2));     // goff
-  add(sizeof(double) * kThreads);     // red
-  add(sizeof(double) * 24);           // dmisc
-  add(sizeof(cplx<T>) * kBK * (kBM + kPad + kBN + kPad));  // tile
-  add(sizeof(cplx<T>) * svd_elems);  // jbuf
-  add(sizeof(cplx<T>) * kMaxVec);     // uvec
-  add(sizeof(int) * (n + 2));         // rdim
-  add(sizeof(T) * 512);               // lam
-  add(sizeof(MpoSpec<T>));
-  return b;
-}
-
-template <typename T>
-__device__ Smem<T> carve(char *base, int n, int W, int svd_elems) {
-  Smem<T> s;
-  size_t b = 0;
-  auto take = [&](size_t bytes) {
-    char *p = base + b;
-    b += (bytes + 15) & ~size_t(15);
-    return p;
-  };
-  s.tx = reinterpret_cast<uint64_t *>(take(sizeof(uint64_t) * 2 * n * W));
-  s.tz = reinterpret_cast<uint64_t *>(take(sizeof(uint64_t) * 2 * n * W));
-  s.ppx = reinterpret_cast<uint64_t *>(take(sizeof(uint64_t) * W));
-  s.ppz = reinterpret_cast<uint64_t *>(take(sizeof(uint64_t) * W));
-  s.tm = reinterpret_cast<uint8_t *>(take(2 * n));
-  s.chi = reinterpret_cast<int *>(take(sizeof(int) * (n + 2)));
-  s.perm = reinterpret_cast<int *>(take(sizeof(int) * 512));
-  s.misc = reinterpret_cast<int *>(take(sizeof(int) * 16));
-  s.off = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (n + 2)));
-  s.goff = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (n + 2)));
-  s.red = reinterpret_cast<double *>(take(sizeof(double) * kThreads));
-  s.dmisc = reinterpret_cast<double *>(take(sizeof(double) * 24));
-  s.tile = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * kBK * (kBM + kPad + kBN + kPad)));
-  s.jbuf = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * svd_elems));
-  s.uvec = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * kMaxVec));
-  s.rdim = reinterpret_cast<int *>(take(sizeof(int) * (n + 2)));
-  s.lam = reinterpret_cast<T *>(take(sizeof(T) * 512));
-  s.spec = reinterpret_cast<MpoSpec<T> *>(take(sizeof(MpoSpec<T>)));
-  return s;
-}
-
-// misc slots
-enum { M_LO = 0, M_HI, M_A, M_B, M_CENTER, M_FAIL, M_KEEP, M_MAXCHI, M_CASEB, M_J, M_BIT, M_LIDX, M_OUTCOME, M_JFLAG };
-// dmisc slots
-enum { D_DISC = 0, D_LOGP, D_E, D_NORM, D_FLOPS = 8, D_PROF = 8 };  // D_PROF + 1 + ProfSlot
-
-// Adds the cycles since `t` to a phase slot and restarts `t` (thread 0 only;
-// callers sit just after a CTA barrier so the CTA is in step).
-__device__ __forceinline__ void prof_mark(double *dmisc, int slot, long long &t) {
-  if (threadIdx.x == 0) {
-    const long long now = clock64();
-    dmisc[D_PROF + 1 + slot] += static_cast<double>(now - t);
-    t = now;
-  }
-}
-
-// Per-CTA scratch partition (complex elements).
-template <typename T>
-struct Scratch {
-  cplx<T> *ap, *g, *t, *y, *h, *v, *vs, *w, *mbuf, *e, *sa, *te;
-  T *lam;
-};
-
-template <typename T>
-__device__ Scratch<T> scratch_for(const EngineParams &P, int cap) {
-  Scratch<T> s;
-  cplx<T> *base = reinterpret_cast<cplx<T> *>(P.scratch) + static_cast<int64_t>(blockIdx.x) * P.scratch_elems;
-  const int64_t c2 = static_cast<int64_t>(cap) * cap;
-  s.ap = base;
-  s.g = s.ap + P.ap_elems;
-  s.t = s.g + P.g_elems;
-  s.y = s.t + 8 * c2;
-  s.h = s.y + 4 * c2;
-  s.v = s.h + 4 * c2;
-  s.vs = s.v + 4 * c2;
-  s.w = s.vs + 4 * c2;
-  s.mbuf = s.w + 2 * c2;
-  s.e = s.mbuf + 4 * c2;
-  s.sa = s.e + c2;
-  s.te = s.sa + 2 * c2;
-  s.lam = reinterpret_cast<T *>(s.te + 2 * c2);
-  return s;
-}
-
-// Algorithmic FLOP counts (real flops of the textbook algorithm, complex = 4
-// real multiply-adds per multiply-add): a GEMM is 8 M N K, a Householder R
-// factor of an m x n matrix 4 (2 m n^2 - 2 n^3 / 3) with m >= n (roles
-// swapped otherwise), the singular values and right vectors of an m x n
-// matrix 4 (4 m n^2 + 8 n^3).
-__device__ __forceinline__ double gemm_flops(int M, int N, int K) { return 8.0 * M * N * K; }
-__device__ __forceinline__ double qr_flops(int m, int n) {
-  double a = m >= n ? m : n, b = m >= n ? n : m;
-  return 4.0 * (2.0 * a * b * b - 2.0 * b * b * b / 3.0);
-}
-__device__ __forceinline__ double svd_flops(int m, int n) {
-  return 4.0 * (4.0 * m * static_cast<double>(n) * n + 8.0 * static_cast<double>(n) * n * n);
-}
-
-// ---------------------------------------------------------------------------
-// MPS pieces (CTA-wide).
-template <typename T>
-__device__ __forceinline__ cplx<T> *site_ptr(const EngineParams &P, int64_t shot, int k) {
-  return reinterpret_cast<cplx<T> *>(P.mps) + shot * P.slab_elems + P.site_off[k];
-}
-
-// out = branch-summed MPO tensor of site k (see header comment): left bond
-// doubled when dl, right bond doubled when dr; the (alpha, l) index is
-// alpha * chl + l.
-template <typename T>
-__device__ void materialize(const MpoSpec<T> &sp, const uint64_t *ppx, const uint64_t *ppz, int k,
-                            const cplx<T> *A, int chl, int chr, bool dl, bool dr, cplx<T> *out) {
-  cplx<T> op0[4], op1[4];
-  site_op(sp, ppx, ppz, k, 0, op0);
-  site_op(sp, ppx, ppz, k, 1, op1);
-  const int Dl = dl ? 2 * chl : chl, Dr = dr ? 2 * chr : chr;
-  const int64_t total = static_cast<int64_t>(Dl) * 2 * Dr;
-  for (int64_t e = tid(); e < total; e += kThreads) {
-    int R = static_cast<int>(e % Dr);
-    int s = static_cast<int>((e / Dr) % 2);
-    int L = static_cast<int>(e / (2 * Dr));
-    int al = dl ? L / chl : -1, l = dl ? L % chl : L;
-    int be = dr ? R / chr : -1, r = dr ? R % chr : R;
-    cplx<T> val = cmake<T>(0, 0);
-    if (!(dl && dr && al != be)) {
-      int br = dl ? al : be;
-      cplx<T> a0 = A[(static_cast<int64_t>(l) * 2 + 0) * chr + r];
-      cplx<T> a1 = A[(static_cast<int64_t>(l) * 2 + 1) * chr + r];
-      if (br < 0) {
-        cfma(val, cadd(op0[s * 2 + 0], op1[s * 2 + 0]), a0);
-        cfma(val, cadd(op0[s * 2 + 1], op1[s * 2 + 1]), a1);
-      } else {
-        const cplx<T> *op = br == 0 ? op0 : op1;
-        cfma(val, op[s * 2 + 0], a0);
-        cfma(val, op[s * 2 + 1], a1);
-      }
-    }
-    out[e] = val;
-  }
-}
-
-// Keep count at one bond from eigenvalues sorted in decreasing order.
-template <typename T>
-__device__ int keep_count(const T *lam_sorted, int n, int cap, double cutoff, double delta) {
-  double s1 = sqrt(fmax(static_cast<double>(lam_sorted[0]), 0.0));
-  if (!(s1 > 0.0)) return 1;
-  int k = 0;
-  for (int i = 0; i < n; ++i)
-    if (sqrt(fmax(static_cast<double>(lam_sorted[i]), 0.0)) > cutoff * s1) ++k;
-  if (k < 1) k = 1;
-  if (k > cap) {
-    double thr = sqrt(fmax(static_cast<double>(lam_sorted[cap]), 0.0)) + delta * s1;
-    int kk = 0;
-    for (int i = 0; i < cap; ++i)
-      if (sqrt(fmax(static_cast<double>(lam_sorted[i]), 0.0)) > thr) ++kk;
-    k = kk < 1 ? 1 : kk;
-  }
-  return k;
-}
-
-// Exact gauge steps (no truncation) moving the orthogonality centre of a
-// shot's MPS from its current site to `target`, so that the sites left of an
-// operator's support are left-canonical and those right of it
-// right-canonical before the operator is applied (Sec. IV B).
-//   Right across site k: A_k as a (2 chi_k) x chi_{k+1} matrix = Q R
-//   (Householder); site k becomes Q (bond k+1 becomes min(2 chi_k,
-//   chi_{k+1})) and A_{k+1} <- R A_{k+1}.
-//   Left across site k: A_k^dag as a (2 chi_{k+1}) x chi_k matrix = Q R;
-//   site k becomes Q^dag and A_{k-1} <- A_{k-1} R^dag.
-template <typename T>
-__device__ void mps_move_center(const EngineParams &P, const Smem<T> &S, int64_t shot, const Scratch<T> &X,
-                                int target) {
-  int *chi = S.chi;
-  const cplx<T> one = cmake<T>(1, 0), zero = cmake<T>(0, 0);
-  int c = S.misc[M_CENTER];
-  while (c < target) {
-    const int l = chi[c], r = chi[c + 1], r2 = chi[c + 2];
-    const int m = 2 * l, steps = min(m, r);
-    if (m > kMaxVec) {
-      if (tid() == 0) S.misc[M_FAIL] = STN_EOVERFLOW;
-      __syncthreads();
-      return;
-    }
-    cplx<T> *A = site_ptr<T>(P, shot, c), *Bn = site_ptr<T>(P, shot, c + 1);
-    for (int e = tid(); e < m * r; e += kThreads) X.t[e] = A[e];
-    __syncthreads();
-    qr_r_inplace<T>(m, r, X.t, r, S.jbuf, P.svd_elems, S.red, S.dmisc + 4, X.h);
-    form_q<T>(m, steps, X.h, X.y, S.jbuf, P.svd_elems);
-    cgemm<T, 0, 0>(steps, 2 * r2, r, one, X.t, r, Bn, 2 * r2, zero, X.w, 2 * r2, S.tile);
-    for (int e = tid(); e < m * steps; e += kThreads) A[e] = X.y[e];
-    for (int e = tid(); e < steps * 2 * r2; e += kThreads) Bn[e] = X.w[e];
-    if (tid() == 0) {
-      chi[c + 1] = steps;
-      S.dmisc[D_FLOPS] += 2.0 * qr_flops(m, r) + gemm_flops(steps, 2 * r2, r);
-      S.dmisc[D_PROF + 1 + PROF_NGAUGE] += 1.0;
-    }
-    __syncthreads();
-    ++c;
-  }
-  while (c > target) {
-    const int l = chi[c], r = chi[c + 1], ll = chi[c - 1];
-    const int m = 2 * r, steps = min(m, l);
-    if (m > kMaxVec) {
-      if (tid() == 0) S.misc[M_FAIL] = STN_EOVERFLOW;
-      __syncthreads();
-      return;
-    }
-    cplx<T> *A = site_ptr<T>(P, shot, c), *Am = site_ptr<T>(P, shot, c - 1);
-    for (int e = tid(); e < m * l; e += kThreads) {
-      const int j = e / l, i = e % l;  // X.t[j][i] = conj(A[i][j]), A as l x 2r
-      X.t[e] = cconj(A[static_cast<int64_t>(i) * m + j]);
-    }
-    __syncthreads();
-    qr_r_inplace<T>(m, l, X.t, l, S.jbuf, P.svd_elems, S.red, S.dmisc + 4, X.h);
-    form_q<T>(m, steps, X.h, X.y, S.jbuf, P.svd_elems);
-    cgemm<T, 0, 1>(2 * ll, steps, l, one, Am, l, X.t, l, zero, X.w, steps, S.tile);
-    for (int e = tid(); e < steps * m; e += kThreads) {
-      const int k = e / m, j = e % m;
-      A[e] = cconj(X.y[static_cast<int64_t>(j) * steps + k]);
-    }
-    for (int e = tid(); e < 2 * ll * steps; e += kThreads) Am[e] = X.w[e];
-    if (tid() == 0) {
-      chi[c] = steps;
-      S.dmisc[D_FLOPS] += 2.0 * qr_flops(m, l) + gemm_flops(2 * ll, steps, l);
-      S.dmisc[D_PROF + 1 + PROF_NGAUGE] += 1.0;
-    }
-    __syncthreads();
-    --c;
-  }
-  if (tid() == 0) S.misc[M_CENTER] = target;
-  __syncthreads();
-}
-
-// Two phases of applying the two-branch MPO `spec` on [lo, hi] and
-// recompressing sites [a, b] (a <= lo <= hi <= b, orthogonality centre inside
-// [a, b]).
-//
-// mps_prepare builds the MPO tensors and runs the left sweep (no truncation
-// yet) and returns the squared norm of the new, untruncated state: for a
-// measurement projector this is the Born probability of the branch, obtained
-// from R factors whose small entries carry absolute (not relative) rounding,
-// so a small probability keeps its relative accuracy (about eps / sqrt(p)).
-// mps_finish then runs the truncating right sweep; the centre ends at a and the
-// state is renormalised.
-template <typename T>
-__device__ double mps_prepare(const EngineParams &P, const Smem<T> &S, int64_t shot,
-                              const Scratch<T> &X, int a, int b) {
-  const MpoSpec<T> &sp = *S.spec;
-  int *chi = S.chi;
-  if (a == b) {
-    cplx<T> *A = site_ptr<T>(P, shot, a);
-    materialize(sp, S.ppx, S.ppz, a, A, chi[a], chi[a + 1], false, false, X.t);
-    __syncthreads();
-    const int64_t tot = static_cast<int64_t>(chi[a]) * 2 * chi[a + 1];
-    double nrm = 0;
-    for (int64_t e = tid(); e < tot; e += kThreads) nrm += static_cast<double>(cabs2(X.t[e]));
-    return block_sum(nrm, S.red);
-  }
-  // doubled bond dimensions D[k] for bonds a..b+1
-  auto Dbond = [&](int k) { return (k > sp.lo && k <= sp.hi) ? 2 * chi[k] : chi[k]; };
-  if (tid() == 0) {
-    int64_t o = 0;
-    for (int k = a; k <= b; ++k) {
-      S.off[k - a] = o;
-      o += static_cast<int64_t>(Dbond(k)) * 2 * Dbond(k + 1);
-    }
-    S.off[b - a + 1] = o;
-    int64_t g = 0;
-    for (int k = a + 1; k <= b; ++k) {
-      S.goff[k - a] = g;
-      g += static_cast<int64_t>(Dbond(k)) * Dbond(k);
-    }
-    S.goff[b - a + 1] = g;
-    if (o > P.ap_elems || g > P.g_elems) S.misc[M_FAIL] = STN_EOVERFLOW;
-  }
-  __syncthreads();
-  if (S.misc[M_FAIL]) return 0.0;
-  for (int k = a; k <= b; ++k) {
-    bool in = k >= sp.lo && k <= sp.hi;
-    bool dl = in && k > sp.lo, dr = in && k < sp.hi;
-    cplx<T> *A = site_ptr<T>(P, shot, k);
-    cplx<T> *out = X.ap + S.off[k - a];
-    if (in) {
-      materialize(sp, S.ppx, S.ppz, k, A, chi[k], chi[k + 1], dl, dr, out);
-    } else {
-      const int64_t tot = static_cast<int64_t>(chi[k]) * 2 * chi[k + 1];
-      for (int64_t e = tid(); e < tot; e += kThreads) out[e] = A[e];
-    }
-  }
-  __syncthreads();
-  const cplx<T> one = cmake<T>(1, 0), zero = cmake<T>(0, 0);
-  const int cap = P.chi_cap;
-  (void)cap;
-  // left sweep: R factor of the left part through site k, for k = a..b-1
-  // (R at bond a is the identity: sites left of a are left-canonical).
-  for (int k = a; k < b; ++k) {
-    const int Dl = Dbond(k), Dr = Dbond(k + 1);
-    const cplx<T> *Ak = X.ap + S.off[k - a];
-    int m;
-    if (k == a) {
-      m = 2 * Dl;
-      const int64_t tot = static_cast<int64_t>(m) * Dr;
-      for (int64_t e = tid(); e < tot; e += kThreads) X.t[e] = Ak[e];
-      __syncthreads();
-    } else {
-      const int r = S.rdim[k - a];
-      const cplx<T> *Rk = X.g + S.goff[k - a];
-      cgemm<T, 0, 0>(r, 2 * Dr, Dl, one, Rk, Dl, Ak, 2 * Dr, zero, X.t, 2 * Dr, S.tile);
-      if (tid() == 0) S.dmisc[D_FLOPS] += gemm_flops(r, 2 * Dr, Dl);
-      m = 2 * r;
-    }
-    if (m > kMaxVec) {
-      if (tid() == 0) S.misc[M_FAIL] = STN_EOVERFLOW;
-      __syncthreads();
-      return 0.0;
-    }
-    qr_r_inplace<T>(m, Dr, X.t, Dr, S.jbuf, P.svd_elems, S.red, S.dmisc + 4);
-    if (tid() == 0) S.dmisc[D_FLOPS] += qr_flops(m, Dr);
-    const int rn = min(m, Dr);
-    cplx<T> *Rout = X.g + S.goff[k + 1 - a];
-    for (int e = tid(); e < rn * Dr; e += kThreads) Rout[e] = X.t[e];
-    if (tid() == 0) S.rdim[k + 1 - a] = rn;
-    __syncthreads();
-  }
-  // squared norm: || R_b A'_b ||_F^2 (the right part beyond b is right-canonical)
-  {
-    const int Dl = Dbond(b), n2 = 2 * Dbond(b + 1), r = S.rdim[b - a];
-    cgemm<T, 0, 0>(r, n2, Dl, one, X.g + S.goff[b - a], Dl, X.ap + S.off[b - a], n2, zero, X.y, n2, S.tile);
-    double nrm = 0;
-    for (int e = tid(); e < r * n2; e += kThreads) nrm += static_cast<double>(cabs2(X.y[e]));
-    return block_sum(nrm, S.red);
-  }
-}
-
-template <typename T>
-__device__ void mps_finish(const EngineParams &P, const Smem<T> &S, int64_t shot, const Scratch<T> &X,
-                           int a, int b) {
-  const MpoSpec<T> &sp = *S.spec;
-  int *chi = S.chi;
-  const int cap = P.chi_cap;
-  if (S.misc[M_FAIL]) return;
-  if (a == b) {
-    cplx<T> *A = site_ptr<T>(P, shot, a);
-    const int64_t tot = static_cast<int64_t>(chi[a]) * 2 * chi[a + 1];
-    double nrm = 0;
-    for (int64_t e = tid(); e < tot; e += kThreads) nrm += static_cast<double>(cabs2(X.t[e]));
-    nrm = block_sum(nrm, S.red);
-    T inv = static_cast<T>(nrm > 0 ? 1.0 / sqrt(nrm) : 0.0);
-    for (int64_t e = tid(); e < tot; e += kThreads) A[e] = cscale(X.t[e], inv);
-    if (tid() == 0) {
-      if (!(nrm > 0) || !isfinite(nrm)) S.misc[M_FAIL] = STN_ENUMERIC;
-      S.misc[M_CENTER] = a;
-    }
-    __syncthreads();
-    return;
-  }
-  auto Dbond = [&](int k) { return (k > sp.lo && k <= sp.hi) ? 2 * chi[k] : chi[k]; };
-  const cplx<T> one = cmake<T>(1, 0), zero = cmake<T>(0, 0);
-  long long tp = clock64();
-  // right sweep
-  int kappa = Dbond(b + 1);
-  const cplx<T> *M = X.ap + S.off[b - a];
-  for (int k = b; k > a; --k) {
-    const int Dl = Dbond(k);
-    const int n2 = 2 * kappa;
-    const int r = S.rdim[k - a];
-    const cplx<T> *Rk = X.g + S.goff[k - a];
-    // C = R_k M (r x n2), then its SVD
-    cgemm<T, 0, 0>(r, n2, Dl, one, Rk, Dl, M, n2, zero, X.y, n2, S.tile);
-    prof_mark(S.dmisc, PROF_RIGHT, tp);
-    const bool in_smem = r * n2 + n2 * n2 <= P.svd_elems;
-    cplx<T> *Cc = in_smem ? S.jbuf : X.h;
-    cplx<T> *Vc = in_smem ? S.jbuf + r * n2 : X.v;
-    // In the complex64 path a bond whose SVD fits shared memory in complex128
-    // is decomposed in double precision: FP32 Jacobi rotations leave the small
-    // singular directions with an absolute error of about sqrt(#rotations)
-    // eps sigma_1, which would be dropped or kept wrongly at every sweep.
-    bool svd64 = false, vec_from_columns = false;
-    if constexpr (sizeof(T) == 4) svd64 = 2 * (r * n2 + n2 * n2) <= P.svd_elems;
-    if (svd64) {
-      cplx<double> *Cd = reinterpret_cast<cplx<double> *>(S.jbuf), *Vd = Cd + r * n2;
-      double *sd = reinterpret_cast<double *>(X.te);
-      for (int e = tid(); e < r * n2; e += kThreads) {
-        int i = e / n2, j = e % n2;
-        cplx<T> v = X.y[e];
-        Cd[j * r + i] = cmake<double>(static_cast<double>(v.re), static_cast<double>(v.im));
-      }
-      __syncthreads();
-      svd_onesided<double>(r, n2, Cd, Vd, sd, &S.misc[M_JFLAG], S.red);
-      for (int e = tid(); e < n2 * n2; e += kThreads)
-        X.v[e] = cmake<T>(static_cast<T>(Vd[e].re), static_cast<T>(Vd[e].im));
-      for (int i = tid(); i < n2; i += kThreads) X.lam[i] = static_cast<T>(sd[i]);
-      __syncthreads();
-      Vc = X.v;
-    } else if (in_smem) {
-      for (int e = tid(); e < r * n2; e += kThreads) {
-        int i = e / n2, j = e % n2;
-        Cc[j * r + i] = X.y[e];
-      }
-      __syncthreads();
-      svd_onesided<T>(r, n2, Cc, Vc, X.lam, &S.misc[M_JFLAG], S.red);
-    } else {
-      // Large bond: C = Q1 R1 (Householder), then one-sided Jacobi on
-      // X = R1^dag (n2 x kx), whose columns converge in a few sweeps because
-      // R1 is already nearly diagonal.  X V_x = U_x Sigma gives
-      // R1 = V_x Sigma U_x^dag, so the right singular vectors of C are the
-      // normalised columns of the rotated X and no rotation is accumulated.
-      // Rows of R1 (row-major, ld n2) are the conjugated columns of X
-      // (column-major, ld n2) in place.
-      if (r > kMaxVec) {
-        if (tid() == 0) S.misc[M_FAIL] = STN_EOVERFLOW;
-        __syncthreads();
-        return;
-      }
-      qr_r_inplace<T>(r, n2, X.y, n2, S.jbuf, P.svd_elems, S.red, S.dmisc + 4);
-      const int kx = min(r, n2);
-      const bool x_smem = n2 * kx <= P.svd_elems;
-      cplx<T> *Xc = x_smem ? S.jbuf : X.y;
-      for (int e = tid(); e < n2 * kx; e += kThreads) Xc[e] = cconj(X.y[e]);
-      __syncthreads();
-      if (x_smem) svd_onesided<T>(n2, kx, Xc, nullptr, X.lam, &S.misc[M_JFLAG], S.red);
-      else svd_onesided_blocked<T>(n2, kx, Xc, nullptr, X.lam, &S.misc[M_JFLAG], S.red, S.jbuf, P.svd_elems);
-      for (int i = kx + tid(); i < n2; i += kThreads) X.lam[i] = T(0);
-      __syncthreads();
-      Vc = Xc;
-      vec_from_columns = true;
-    }
-    __syncthreads();
-    prof_mark(S.dmisc, PROF_SVD, tp);
-    if (tid() == 0) {
-      S.dmisc[D_FLOPS] += gemm_flops(r, n2, Dl) + svd_flops(r, n2);
-      S.dmisc[D_PROF + 1 + (vec_from_columns ? PROF_NSVD_LARGE : PROF_NSVD_SMALL)] += 1.0;
-    }
-    for (int i = tid(); i < n2; i += kThreads) {
-      if (!isfinite(static_cast<double>(X.lam[i]))) {
-        S.misc[M_FAIL] = STN_ENUMERIC;
-        X.lam[i] = T(0);
-      }
-    }
-    __syncthreads();
-    if (S.misc[M_FAIL]) return;
-    sort_desc<T>(n2, X.lam, S.perm);
-    for (int i = tid(); i < n2; i += kThreads) S.lam[i] = X.lam[S.perm[i]];
-    __syncthreads();
-    if (tid() == 0) {
-      int kmax = min(cap, P.chimax[k]);
-      int keep = keep_count<T>(S.lam, n2, kmax, P.cutoff, P.delta);
-      if (keep > kmax) keep = kmax;
-      double tot = 0, drop = 0;
-      for (int i = 0; i < n2; ++i) {
-        double l = fmax(static_cast<double>(S.lam[i]), 0.0);
-        tot += l;
-        if (i >= keep) drop += l;
-      }
-      if (tot > 0) S.dmisc[D_DISC] += drop / tot;
-      S.misc[M_KEEP] = keep;
-    }
-    __syncthreads();
-    const int keep = S.misc[M_KEEP];
-    // sorted, kept right singular vectors: Vs[:, c] = V[:, perm[c]], c < keep
-    // (or the rotated column of X over its norm)
-    for (int e = tid(); e < n2 * keep; e += kThreads) {
-      int i = e / keep, c = e % keep;
-      cplx<T> v = Vc[static_cast<int64_t>(S.perm[c]) * n2 + i];
-      if (vec_from_columns) {
-        T l = S.lam[c];
-        v = l > T(0) ? cscale(v, T(1) / sqrt(l)) : cmake<T>(i == c ? T(1) : T(0), 0);
-      }
-      X.vs[i * keep + c] = v;
-    }
-    __syncthreads();
-    reorthonormalize<T>(n2, keep, X.vs, X.e, X.y, S.tile);
-    // new right-canonical site k: B[c][s][r] = conj(Vs[(s*kappa + r)][c])
-    cplx<T> *Bk = site_ptr<T>(P, shot, k);
-    for (int e = tid(); e < keep * n2; e += kThreads) {
-      int c = e / n2, sr = e % n2;
-      Bk[e] = cconj(X.vs[sr * keep + c]);
-    }
-    // W = M Vs (Dl x keep)
-    cgemm<T, 0, 0>(Dl, keep, n2, one, M, n2, X.vs, keep, zero, X.w, keep, S.tile);
-    // M_{k-1} = A'_{k-1} (left reshape 2D_{k-1} x Dl) W
-    const int Dll = Dbond(k - 1);
-    const cplx<T> *Akm1 = X.ap + S.off[k - 1 - a];
-    cgemm<T, 0, 0>(2 * Dll, keep, Dl, one, Akm1, Dl, X.w, keep, zero, X.mbuf, keep, S.tile);
-    if (tid() == 0) {
-      chi[k] = keep;
-      S.dmisc[D_FLOPS] += gemm_flops(Dl, keep, n2) + gemm_flops(2 * Dll, keep, Dl);
-    }
-    __syncthreads();
-    M = X.mbuf;
-    kappa = keep;
-  }
-  prof_mark(S.dmisc, PROF_RIGHT, tp);
-  // centre site a = M (chi[a] x 2 x kappa), renormalised
-  cplx<T> *Aa = site_ptr<T>(P, shot, a);
-  const int64_t tot = static_cast<int64_t>(chi[a]) * 2 * kappa;
-  double nrm = 0;
-  for (int64_t e = tid(); e < tot; e += kThreads) nrm += static_cast<double>(cabs2(M[e]));
-  nrm = block_sum(nrm, S.red);
-  T inv = static_cast<T>(nrm > 0 ? 1.0 / sqrt(nrm) : 0.0);
-  for (int64_t e = tid(); e < tot; e += kThreads) Aa[e] = cscale(M[e], inv);
-  if (tid() == 0) {
-    if (!(nrm > 0) || !isfinite(nrm)) S.misc[M_FAIL] = STN_ENUMERIC;
-    S.misc[M_CENTER] = a;
-    int mx = S.misc[M_MAXCHI];
-    for (int k = a + 1; k <= b; ++k) mx = max(mx, chi[k]);
-    S.misc[M_MAXCHI] = mx;
-  }
-  __syncthreads();
-}
-
-// <phi| i^m X^x Z^z |phi> over sites [a, b] (centre inside, so the rest of
-// the chain contracts to the identity).  Returns the real part.
-template <typename T>
-__device__ double mps_expect(const EngineParams &P, const Smem<T> &S, int64_t shot,
-                             const Scratch<T> &X, int a, int b, int m) {
-  const int *chi = S.chi;
-  const cplx<T> one = cmake<T>(1, 0), zero = cmake<T>(0, 0);
-  MpoSpec<T> sp;
-  sp.kind = MPO_ROT; sp.lo = -1; sp.hi = -1; sp.j = -1;
-  sp.w0 = one; sp.w1 = one; sp.v0 = zero; sp.v1 = zero;
-  for (int k = a; k <= b; ++k) {
-    const cplx<T> *A = site_ptr<T>(P, shot, k);
-    const int cl = chi[k], cr = chi[k + 1];
-    // SA = (X^x Z^z)_k A_k
-    cplx<T> op[4];
-    site_op(sp, S.ppx, S.ppz, k, 1, op);
-    const int64_t tot = static_cast<int64_t>(cl) * 2 * cr;
-    for (int64_t e = tid(); e < tot; e += kThreads) {
-      int r = static_cast<int>(e % cr), s = static_cast<int>((e / cr) % 2);
-      int64_t l = e / (2 * cr);
-      cplx<T> v = cmake<T>(0, 0);
-      cfma(v, op[s * 2 + 0], A[(l * 2 + 0) * cr + r]);
-      cfma(v, op[s * 2 + 1], A[(l * 2 + 1) * cr + r]);
-      X.sa[e] = v;
-    }
-    __syncthreads();
-    if (k == a) {
-      cgemm<T, 1, 0>(cr, cr, 2 * cl, one, A, cr, X.sa, cr, zero, X.e, cr, S.tile);
-      if (tid() == 0) S.dmisc[D_FLOPS] += gemm_flops(cr, cr, 2 * cl);
-    } else {
-      cgemm<T, 0, 0>(cl, 2 * cr, cl, one, X.e, cl, X.sa, 2 * cr, zero, X.te, 2 * cr, S.tile);
-      cgemm<T, 1, 0>(cr, cr, 2 * cl, one, A, cr, X.te, cr, zero, X.e, cr, S.tile);
-      if (tid() == 0) S.dmisc[D_FLOPS] += gemm_flops(cl, 2 * cr, cl) + gemm_flops(cr, cr, 2 * cl);
-    }
-  }
-  const int cb = chi[b + 1];
-  double re = 0, im = 0;
-  for (int i = tid(); i < cb; i += kThreads) {
-    re += static_cast<double>(X.e[i * cb + i].re);
-    im += static_cast<double>(X.e[i * cb + i].im);
-  }
-  re = block_sum(re, S.red);
-  im = block_sum(im, S.red);
-  // multiply by i^m, keep the real part
-  switch (m & 3) {
-    case 0: return re;
-    case 1: return -im;
-    case 2: return -re;
-    default: return im;
-  }
-}
-
-// The same contraction in double precision from the (single-precision) site
-// tensors, for spans whose bonds are all <= kExpect64Chi: shared-memory
-// buffers only.  Used by the complex64 path so that Born probabilities keep
-// double accuracy where it is cheap.
-constexpr int kExpect64Chi = 32;
-
-template <typename T>
-__device__ double mps_expect64(const EngineParams &P, const Smem<T> &S, int64_t shot, int a, int b, int m) {
-  const int *chi = S.chi;
-  const int c = kExpect64Chi, c2 = c * c;
-  cplx<double> *E = reinterpret_cast<cplx<double> *>(S.jbuf);
-  cplx<double> *SA = E + c2, *TE = SA + 2 * c2, *AD = TE + 2 * c2;
-  cplx<double> *tile = AD + 2 * c2;
-  const cplx<double> one = cmake<double>(1, 0), zero = cmake<double>(0, 0);
-  MpoSpec<double> sp;
-  sp.kind = MPO_ROT; sp.lo = -1; sp.hi = -1; sp.j = -1;
-  sp.w0 = one; sp.w1 = one; sp.v0 = zero; sp.v1 = zero;
-  for (int k = a; k <= b; ++k) {
-    const cplx<T> *A = site_ptr<T>(P, shot, k);
-    const int cl = chi[k], cr = chi[k + 1];
-    cplx<double> op[4];
-    site_op(sp, S.ppx, S.ppz, k, 1, op);
-    const int tot = cl * 2 * cr;
-    for (int e = tid(); e < tot; e += kThreads) {
-      cplx<T> v = A[e];
-      AD[e] = cmake<double>(static_cast<double>(v.re), static_cast<double>(v.im));
-    }
-    __syncthreads();
-    for (int e = tid(); e < tot; e += kThreads) {
-      int r = e % cr, s = (e / cr) % 2, l = e / (2 * cr);
-      cplx<double> v = cmake<double>(0, 0);
-      cfma(v, op[s * 2 + 0], AD[(l * 2 + 0) * cr + r]);
-      cfma(v, op[s * 2 + 1], AD[(l * 2 + 1) * cr + r]);
-      SA[e] = v;
-    }
-    __syncthreads();
-    if (k == a) {
-      cgemm<double, 1, 0>(cr, cr, 2 * cl, one, AD, cr, SA, cr, zero, E, cr, tile);
-    } else {
-      cgemm<double, 0, 0>(cl, 2 * cr, cl, one, E, cl, SA, 2 * cr, zero, TE, 2 * cr, tile);
-      cgemm<double, 1, 0>(cr, cr, 2 * cl, one, AD, cr, TE, cr, zero, E, cr, tile);
-    }
-  }
-  const int cb = chi[b + 1];
-  double re = 0, im = 0;
-  for (int i = tid(); i < cb; i += kThreads) {
-    re += E[i * cb + i].re;
-    im += E[i * cb + i].im;
-  }
-  re = block_sum(re, S.red);
-  im = block_sum(im, S.red);
-  switch (m & 3) {
-    case 0: return re;
-    case 1: return -im;
-    case 2: return -re;
-    default: return im;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Tableau helpers (shared memory, one thread unless noted).
-__device__ __forceinline__ int popc64(uint64_t v) { return __popcll(v); }
-
-// row r <- row r * row s (Pauli product with the exact phase)
-__device__ void row_mul(uint64_t *tx, uint64_t *tz, uint8_t *tm, int W, int r, int s) {
-  int sw = 0;
-  for (int w = 0; w < W; ++w) {
-    sw += popc64(tz[r * W + w] & tx[s * W + w]);
-    tx[r * W + w] ^= tx[s * W + w];
-    tz[r * W + w] ^= tz[s * W + w];
-  }
-  tm[r] = static_cast<uint8_t>((tm[r] + tm[s] + 2 * sw) & 3);
-}
-
-// rows of X errors anticommute with Z_q, and vice versa
-__device__ void pauli_left(uint8_t *tm, int n, int q, int letter /*1 X, 2 Y, 3 Z*/) {
-  if (letter == 1 || letter == 2) tm[n + q] = static_cast<uint8_t>((tm[n + q] + 2) & 3);
-  if (letter == 3 || letter == 2) tm[q] = static_cast<uint8_t>((tm[q] + 2) & 3);
-}
-
-// P' = row r1 * row r2 (r2 < 0: just row r1) into ppx/ppz, phase returned
-__device__ int conj_rows(const uint64_t *tx, const uint64_t *tz, const uint8_t *tm, int W, int r1,
-                         int r2, uint64_t *ppx, uint64_t *ppz) {
-  int m = tm[r1];
-  int sw = 0;
-  for (int w = 0; w < W; ++w) {
-    ppx[w] = tx[r1 * W + w];
-    ppz[w] = tz[r1 * W + w];
-    if (r2 >= 0) {
-      sw += popc64(ppz[w] & tx[r2 * W + w]);
-      ppx[w] ^= tx[r2 * W + w];
-      ppz[w] ^= tz[r2 * W + w];
-    }
-  }
-  if (r2 >= 0) m += tm[r2] + 2 * sw;
-  return m & 3;
-}
-
-// Single-qubit Clifford L applied to the site-j letter of every row:
-// R -> L R L^dag, for the four L that take the measured eigenvector to |0>:
-// index 0: X,+1 (H)  1: X,-1 (X H)  2: Y,+1 (H S^dag)  3: Y,-1 (X H S^dag).
-// Table: [L][xz] -> (x', z', dm) with xz = 2x + z.
-__constant__ uint8_t kLTable[4][4][3] = {
-    {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {1, 1, 2}},
-    {{0, 0, 0}, {1, 0, 0}, {0, 1, 2}, {1, 1, 0}},
-    {{0, 0, 0}, {1, 0, 0}, {1, 1, 1}, {0, 1, 3}},
-    {{0, 0, 0}, {1, 0, 0}, {1, 1, 3}, {0, 1, 1}},
-};
-
-// C <- C U L^dag for U = prod_{k != j} controlled-P'_k (control j): every row
-// R -> L (U R U) L^dag, with U R U = R Z_j^a (x_j(R) = 0) or
-// (-1)^a R Z_j^a Q (x_j(R) = 1), a = [R anticommutes with Q],
-// Q = prod_{k != j} P'_k.  CTA-wide over rows.
-__device__ void tableau_caseB(uint64_t *tx, uint64_t *tz, uint8_t *tm, int n, int W,
-                              const uint64_t *ppx, const uint64_t *ppz, int j, int lidx) {
-  const int jw = j >> 6;
-  const uint64_t jb = 1ull << (j & 63);
-  for (int r = tid(); r < 2 * n; r += kThreads) {
-    int an = 0, mq = 0;
-    for (int w = 0; w < W; ++w) {
-      uint64_t xq = ppx[w] & (w == jw ? ~jb : ~0ull);
-      uint64_t zq = ppz[w] & (w == jw ? ~jb : ~0ull);
-      an += popc64((tx[r * W + w] & zq) ^ (tz[r * W + w] & xq));
-      mq += popc64(xq & zq);
-    }
-    an &= 1;
-    const bool xj = (tx[r * W + jw] & jb) != 0;
-    int m = tm[r];
-    if (an) tz[r * W + jw] ^= jb;
-    if (xj) {
-      if (an) m += 2;
-      int sw = 0;
-      for (int w = 0; w < W; ++w) {
-        uint64_t xq = ppx[w] & (w == jw ? ~jb : ~0ull);
-        uint64_t zq = ppz[w] & (w == jw ? ~jb : ~0ull);
-        sw += popc64(tz[r * W + w] & xq);
-        tx[r * W + w] ^= xq;
-        tz[r * W + w] ^= zq;
-      }
-      m += mq + 2 * sw;
-    }
-    int x = (tx[r * W + jw] & jb) ? 1 : 0, z = (tz[r * W + jw] & jb) ? 1 : 0;
-    const uint8_t *e = kLTable[lidx][2 * x + z];
-    if (e[0]) tx[r * W + jw] |= jb; else tx[r * W + jw] &= ~jb;
-    if (e[1]) tz[r * W + jw] |= jb; else tz[r * W + jw] &= ~jb;
-    tm[r] = static_cast<uint8_t>((m + e[2]) & 3);
-  }
-  __syncthreads();
-}
-
-// Projector MPO of outcome `bit` for the measured P' (thread 0): case A
-// (no X or Y in P') projects with (I + (-1)^bit P')/2; case B applies the
-// controlled-Pauli product with the site-j projection onto the lambda
-// eigenvector, lambda = (-1)^bit * sign(P').
-template <typename T>
-__device__ void set_meas_spec(const Smem<T> &S, int bit) {
-  MpoSpec<T> &sp = *S.spec;
-  const int mb = S.misc[M_BIT];
-  const int m = mb & 3;
-  const int neg = (mb >> 4) & 1;
-  if (!S.misc[M_CASEB]) {
-    sp.kind = MPO_PROJ_Z;
-    sp.w0 = cmake<T>(T(0.5), 0);
-    cplx<T> w1 = ipow<T>(m);
-    T sgn = bit ? T(-0.5) : T(0.5);
-    sp.w1 = cmake<T>(w1.re * sgn, w1.im * sgn);
-  } else {
-    const int jq = S.misc[M_J];
-    const bool zj = (S.ppz[jq >> 6] >> (jq & 63)) & 1;
-    int lam = (bit ? -1 : 1) * (neg ? -1 : 1);
-    const T r2 = static_cast<T>(0.70710678118654752440);
-    sp.kind = MPO_PROJ_B;
-    sp.w0 = cmake<T>(1, 0);
-    sp.w1 = cmake<T>(1, 0);
-    sp.v0 = cmake<T>(r2, 0);
-    sp.v1 = zj ? cmake<T>(0, lam > 0 ? r2 : -r2) : cmake<T>(lam > 0 ? r2 : -r2, 0);
-    S.misc[M_LIDX] = (zj ? 2 : 0) + (lam < 0 ? 1 : 0);
-  }
-}
-
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
-  extern __shared__ __align__(16) char smem_raw[];
-  const int n = P.n, W = P.W;
-  Smem<T> S = carve<T>(smem_raw, n, W, P.svd_elems);
-  Scratch<T> X = scratch_for<T>(P, P.work_c);
-  for (int64_t shot = blockIdx.x; shot < P.shots; shot += gridDim.x) {
-    // load the frame and the MPS bookkeeping
-    for (int e = tid(); e < 2 * n * W; e += kThreads) {
-      S.tx[e] = P.tab_x[shot * 2 * n * W + e];
-      S.tz[e] = P.tab_z[shot * 2 * n * W + e];
-    }
-    for (int e = tid(); e < 2 * n; e += kThreads) S.tm[e] = P.tab_m[shot * 2 * n + e];
-    for (int e = tid(); e <= n; e += kThreads) S.chi[e] = P.chi[shot * (n + 1) + e];
-    if (tid() == 0) {
-      S.misc[M_CENTER] = P.center[shot];
-      S.misc[M_FAIL] = P.status[shot];
-      S.misc[M_MAXCHI] = P.maxchi[shot];
-      S.dmisc[D_DISC] = P.disc[shot];
-      S.dmisc[D_LOGP] = P.logp[shot];
-      S.dmisc[D_FLOPS] = 0.0;
-      for (int i = 0; i < kProfSlots - 1; ++i) S.dmisc[D_PROF + 1 + i] = 0.0;
-    }
-    __syncthreads();
-    long long t_ops = clock64();
-    const uint64_t gshot = P.shot_offset + static_cast<uint64_t>(shot);
-    for (int oi = P.op_begin; oi < P.op_end; ++oi) {
-      if (S.misc[M_FAIL]) break;
-      const Op op = P.ops[oi];
-      switch (op.kind) {
-        case OP_RESET_FLIP:
-          if (tid() == 0 && philox_uniform(P.seed, gshot, op.ev) < P.pR) pauli_left(S.tm, n, op.a, 1);
-          break;
-        case OP_H:
-          if (tid() < W) {
-            int w = tid();
-            uint64_t t = S.tx[op.a * W + w];
-            S.tx[op.a * W + w] = S.tx[(n + op.a) * W + w];
-            S.tx[(n + op.a) * W + w] = t;
-            t = S.tz[op.a * W + w];
-            S.tz[op.a * W + w] = S.tz[(n + op.a) * W + w];
-            S.tz[(n + op.a) * W + w] = t;
-          }
-          if (tid() == 0) {
-            uint8_t t = S.tm[op.a];
-            S.tm[op.a] = S.tm[n + op.a];
-            S.tm[n + op.a] = t;
-          }
-          break;
-        case OP_NOISE1:
-          if (tid() == 0) {
-            double u = philox_uniform(P.seed, gshot, op.ev);
-            if (u < P.p1) pauli_left(S.tm, n, op.a, 1 + min(2, static_cast<int>(3.0 * u / P.p1)));
-          }
-          break;
-        case OP_CNOT:
-          if (tid() == 0) {
-            row_mul(S.tx, S.tz, S.tm, W, op.a, op.b);          // X_c <- X_c X_t
-            row_mul(S.tx, S.tz, S.tm, W, n + op.b, n + op.a);  // Z_t <- Z_t Z_c (rows commute)
-          }
-          break;
-        case OP_NOISE2:
-          if (tid() == 0) {
-            double u = philox_uniform(P.seed, gshot, op.ev);
-            if (u < P.p2) {
-              int idx = min(14, static_cast<int>(15.0 * u / P.p2)) + 1;
-              int lc = idx / 4, lt = idx % 4;  // 0 I, 1 X, 2 Y, 3 Z
-              if (lc) pauli_left(S.tm, n, op.a, lc);
-              if (lt) pauli_left(S.tm, n, op.b, lt);
-            }
-          }
-          break;
-        case OP_ROT:
-        case OP_MEAS: {
-          const bool meas = op.kind == OP_MEAS;
-          if (tid() == 0) {
-            int m;
-            if (meas) m = conj_rows(S.tx, S.tz, S.tm, W, n + op.a, -1, S.ppx, S.ppz);
-            else if (op.pauli == 0) m = conj_rows(S.tx, S.tz, S.tm, W, n + op.a, n + op.b, S.ppx, S.ppz);
-            else m = conj_rows(S.tx, S.tz, S.tm, W, op.a, op.b, S.ppx, S.ppz);
-            int lo = n, hi = -1, j = -1, xany = 0, xz = 0;
-            for (int q = 0; q < n; ++q) {
-              bool x = (S.ppx[q >> 6] >> (q & 63)) & 1, z = (S.ppz[q >> 6] >> (q & 63)) & 1;
-              if (x || z) { lo = min(lo, q); hi = max(hi, q); }
-              if (x && j < 0) j = q;
-              xany |= x;
-              xz += x && z;
-            }
-            int c = S.misc[M_CENTER];
-            S.misc[M_LO] = lo;
-            S.misc[M_HI] = hi;
-            (void)c;
-            S.misc[M_A] = lo;
-            S.misc[M_B] = hi;
-            S.misc[M_J] = j;
-            S.misc[M_CASEB] = xany;
-            S.misc[M_BIT] = m | ((((m - xz) & 3) == 2) << 4);  // phase | (sign < 0) << 4
-            MpoSpec<T> &sp = *S.spec;
-            sp.lo = lo; sp.hi = hi; sp.j = j;
-            if (!meas) {
-              double th = P.theta[op.idx];
-              cplx<T> w1 = cmul(cmake<T>(0, static_cast<T>(-sin(th))), ipow<T>(m));
-              sp.kind = MPO_ROT;
-              sp.w0 = cmake<T>(static_cast<T>(cos(th)), 0);
-              sp.w1 = w1;
-            }
-            if (lo > hi) S.misc[M_FAIL] = STN_ENUMERIC;  // identity Pauli cannot occur
-          }
-          __syncthreads();
-          if (S.misc[M_FAIL]) break;
-          const int a = S.misc[M_A], b = S.misc[M_B];
-          {
-            // the centre moves into [a, b] by exact gauge steps; the sweep
-            // then covers the operator's support only
-            const int c0 = S.misc[M_CENTER];
-            const int tgt = c0 < a ? a : (c0 > b ? b : c0);
-            if (tgt != c0) {
-              long long tg = clock64();
-              mps_move_center<T>(P, S, shot, X, tgt);
-              prof_mark(S.dmisc, PROF_GAUGE, tg);
-            }
-          }
-          if (S.misc[M_FAIL]) break;
-          int caseB = 0, lidx = 0, outcome = 0;
-          if (meas) {
-            // The Born probability of the less likely branch is taken from the
-            // norm of its projected state (accurate for small p); the FP32
-            // expectation value only decides which branch that is.
-            const int mb = S.misc[M_BIT];
-            bool exact64 = false;
-            if constexpr (sizeof(T) == 4) {
-              constexpr size_t need = sizeof(cplx<double>) * (7 * kExpect64Chi * kExpect64Chi +
-                                                              kBK * (kBM + kPad + kBN + kPad));
-              int mx = 1;
-              for (int k = a; k <= b + 1; ++k) mx = max(mx, S.chi[k]);
-              exact64 = mx <= kExpect64Chi && need <= sizeof(cplx<T>) * static_cast<size_t>(P.svd_elems);
-            }
-            long long tq = clock64();
-            double e = 0.0;
-            if constexpr (sizeof(T) == 4) {
-              if (exact64) e = mps_expect64<T>(P, S, shot, a, b, mb & 3);
-              else e = mps_expect<T>(P, S, shot, X, a, b, mb & 3);
-            } else {
-              e = mps_expect<T>(P, S, shot, X, a, b, mb & 3);
-            }
-            const int small = e >= 0.0 ? 1 : 0;
-            if (tid() == 0) set_meas_spec<T>(S, small);
-            __syncthreads();
-            prof_mark(S.dmisc, PROF_EXPECT, tq);
-            double ps = fmin(1.0, fmax(0.0, mps_prepare<T>(P, S, shot, X, a, b)));
-            prof_mark(S.dmisc, PROF_LEFT, tq);
-            // in double precision the expectation value is as accurate as the
-            // projected norm; in single precision it is preferred only where
-            // it was contracted in double
-            if (exact64) ps = fmin(1.0, fmax(0.0, 0.5 * (1.0 - fabs(e))));
-            if (tid() == 0) {
-              double p0 = small == 0 ? ps : 1.0 - ps;
-              double u = philox_uniform(P.seed, gshot, op.ev);
-              int bit = u < p0 ? 0 : 1;
-              double pb = bit == 0 ? p0 : 1.0 - p0;
-              if (fabs(u - p0) < kNearThreshold) P.near[shot] += 1;
-              P.born[shot * P.n_meas + op.idx] = pb;
-              S.dmisc[D_LOGP] += log(pb);
-              int flip = philox_uniform(P.seed, gshot, op.ev + 1) < P.pM ? 1 : 0;
-              if (bit ^ flip) P.records[shot * P.rec_bytes + op.idx / 8] |= static_cast<uint8_t>(1u << (op.idx % 8));
-              S.misc[M_OUTCOME] = bit;
-              if (bit != small) set_meas_spec<T>(S, bit);
-            }
-            __syncthreads();
-            caseB = S.misc[M_CASEB];
-            lidx = S.misc[M_LIDX];
-            outcome = S.misc[M_OUTCOME];
-            tq = clock64();
-            if (outcome != small) mps_prepare<T>(P, S, shot, X, a, b);
-            __syncthreads();
-            prof_mark(S.dmisc, PROF_LEFT, tq);
-            mps_finish<T>(P, S, shot, X, a, b);
-          } else {
-            long long tq = clock64();
-            mps_prepare<T>(P, S, shot, X, a, b);
-            __syncthreads();
-            prof_mark(S.dmisc, PROF_LEFT, tq);
-            mps_finish<T>(P, S, shot, X, a, b);
-          }
-          if (meas) {
-            if (caseB) tableau_caseB(S.tx, S.tz, S.tm, n, W, S.ppx, S.ppz, S.misc[M_J], lidx);
-            if (tid() == 0 && op.pauli == 1) {
-              if (outcome) pauli_left(S.tm, n, op.a, 1);
-              if (philox_uniform(P.seed, gshot, op.ev + 2) < P.pR) pauli_left(S.tm, n, op.a, 1);
-            }
-          }
-          break;
-        }
-        default:
-          if (tid() == 0) S.misc[M_FAIL] = STN_EINVAL;
-      }
-      __syncthreads();
-    }
-    // store
-    for (int e = tid(); e < 2 * n * W; e += kThreads) {
-      P.tab_x[shot * 2 * n * W + e] = S.tx[e];
-      P.tab_z[shot * 2 * n * W + e] = S.tz[e];
-    }
-    for (int e = tid(); e < 2 * n; e += kThreads) P.tab_m[shot * 2 * n + e] = S.tm[e];
-    for (int e = tid(); e <= n; e += kThreads) P.chi[shot * (n + 1) + e] = S.chi[e];
-    if (tid() == 0) {
-      P.center[shot] = S.misc[M_CENTER];
-      P.status[shot] = S.misc[M_FAIL];
-      P.maxchi[shot] = S.misc[M_MAXCHI];
-      P.disc[shot] = S.dmisc[D_DISC];
-      P.logp[shot] = S.dmisc[D_LOGP];
-      P.flops[shot] += S.dmisc[D_FLOPS];
-      S.dmisc[D_PROF + 1 + PROF_OPS] = static_cast<double>(clock64() - t_ops);
-      for (int i = 0; i < kProfSlots - 1; ++i) P.prof[shot * kProfSlots + i] += S.dmisc[D_PROF + 1 + i];
-      if (S.misc[M_FAIL]) atomicCAS(P.err, 0, S.misc[M_FAIL]);
-    }
-    __syncthreads();
-  }
-}
-
-// Identity frame, |0...0>, cleared records and accumulators.
-template <typename T>
-__global__ void init_kernel(EngineParams P) {
-  const int n = P.n, W = P.W;
-  for (int64_t shot = blockIdx.x; shot < P.shots; shot += gridDim.x) {
-    for (int e = tid(); e < 2 * n * W; e += blockDim.x) {
-      int r = e / W, w = e % W;
-      int q = r % n;
-      uint64_t bit = (q >> 6) == w ? (1ull << (q & 63)) : 0ull;
-      P.tab_x[shot * 2 * n * W + e] = r < n ? bit : 0ull;
-      P.tab_z[shot * 2 * n * W + e] = r < n ? 0ull : bit;
-    }
-    for (int e = tid(); e < 2 * n; e += blockDim.x) P.tab_m[shot * 2 * n + e] = 0;
-    for (int e = tid(); e <= n; e += blockDim.x) P.chi[shot * (n + 1) + e] = 1;
-    cplx<T> *slab = reinterpret_cast<cplx<T> *>(P.mps) + shot * P.slab_elems;
-    for (int k = tid(); k < n; k += blockDim.x) {
-      slab[P.site_off[k]] = cmake<T>(1, 0);
-      slab[P.site_off[k] + 1] = cmake<T>(0, 0);
-    }
-    for (int e = tid(); e < P.rec_bytes; e += blockDim.x) P.records[shot * P.rec_bytes + e] = 0;
-    for (int e = tid(); e < P.n_meas; e += blockDim.x) P.born[shot * P.n_meas + e] = 0.0;
-    if (tid() == 0) {
-      P.center[shot] = 0;
-      P.status[shot] = 0;
-      P.maxchi[shot] = 1;
-      P.near[shot] = 0;
-      P.disc[shot] = 0.0;
-      P.logp[shot] = 0.0;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Kernel-level checks of the dense routines on one CTA (complex elements of
-// precision T, column-major C/V for the SVD, row-major B for the QR).
-template <typename T>
-__global__ void __launch_bounds__(kThreads, 1) dense_check_kernel(int what, int m, int n, cplx<T> *A,
-                                                                  cplx<T> *V, T *sig2, int use_smem) {
-  extern __shared__ __align__(16) char smem_raw[];
-  double *red = reinterpret_cast<double *>(smem_raw);
-  double *dm = red + kThreads;
-  int *flag = reinterpret_cast<int *>(dm + 16);
-  cplx<T> *uv = reinterpret_cast<cplx<T> *>(flag + 16);
-  cplx<T> *buf = uv + kMaxVec;
-  if (what == 0) {
-    qr_r_inplace<T>(m, n, A, n, buf, SvdSmem<T>::elems, red, dm);
-  } else if (use_smem == 3) {
-    // the large-bond path of the truncation sweep: A row-major (m x n),
-    // R factor, Jacobi on X = R^dag (n x k), V = normalised columns of X
-    qr_r_inplace<T>(m, n, A, n, buf, SvdSmem<T>::elems, red, dm);
-    const int k = min(m, n);
-    const bool x_smem = n * k <= SvdSmem<T>::elems;
-    cplx<T> *Xc = x_smem ? buf : A;
-    for (int e = tid(); e < n * k; e += kThreads) Xc[e] = cconj(A[e]);
-    __syncthreads();
-    if (x_smem) svd_onesided<T>(n, k, Xc, nullptr, sig2, flag, red);
-    else svd_onesided_blocked<T>(n, k, Xc, nullptr, sig2, flag, red, buf, SvdSmem<T>::elems);
-    for (int e = tid(); e < n * n; e += kThreads) {
-      const int c = e / n;
-      const T l = c < k ? sig2[c] : T(0);
-      V[e] = l > T(0) ? cscale(Xc[e], T(1) / sqrt(l)) : cmake<T>(0, 0);
-    }
-    for (int c = k + tid(); c < n; c += kThreads) sig2[c] = T(0);
-  } else {
-    cplx<T> *C = A, *VV = V;
-    if (use_smem == 1) {
-      C = buf;
-      VV = buf + m * n;
-      for (int e = tid(); e < m * n; e += kThreads) C[e] = A[e];
-      __syncthreads();
-    }
-    if (use_smem == 2) svd_onesided_blocked<T>(m, n, C, VV, sig2, flag, red, buf, SvdSmem<T>::elems);
-    else svd_onesided<T>(m, n, C, VV, sig2, flag, red);
-    if (use_smem == 1) {
-      for (int e = tid(); e < m * n; e += kThreads) A[e] = C[e];
-      for (int e = tid(); e < n * n; e += kThreads) V[e] = VV[e];
-    }
-  }
-}
-
-template <typename T>
-static cudaError_t launch_dense_check_t(int what, int m, int n, void *A, void *V, void *sig2, int use_smem,
-                                        cudaStream_t s) {
-  size_t smem = sizeof(double) * (kThreads + 16) + sizeof(int) * 16 + sizeof(cplx<T>) * kMaxVec;
-  smem += sizeof(cplx<T>) * SvdSmem<T>::elems;  // QR panel, SVD matrix or staged column blocks
-  cudaError_t e = cudaFuncSetAttribute(dense_check_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
-  dense_check_kernel<T><<<1, kThreads, smem, s>>>(what, m, n, static_cast<cplx<T> *>(A),
-                                                  static_cast<cplx<T> *>(V), static_cast<T *>(sig2), use_smem);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_dense_check(int precision, int what, int m, int n, void *A, void *V, void *sig2,
-                               int use_smem, cudaStream_t s) {
-  return precision == 0 ? launch_dense_check_t<double>(what, m, n, A, V, sig2, use_smem, s)
-                        : launch_dense_check_t<float>(what, m, n, A, V, sig2, use_smem, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -2041,96 +59,6 @@ cudaError_t launch_detectors(const uint8_t *records, int rec_bytes, int64_t shot
   detector_kernel<<<grid, 256, 0, s>>>(records, rec_bytes, shots, det, n_det, logical, n_logical, out_det,
                                        out_obs);
   return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Allocation-free large-bond SVD.  Some callers cannot allocate device memory
-// at the moment they need this routine: code running inside a host callback
-// or under a framework's memory pool that forbids cudaMalloc mid-stream, or an
-// embedded runtime that hands out only the buffers it owns.  For them the work
-// copy of the input lives in this file-scope array instead of a buffer the
-// caller or the library would allocate.  Every GPU that loads the library
-// holds the array until the process exits.  All calls share it: it keeps the
-// last call's contents, and two calls that overlap on the GPU (different
-// streams, or different host threads on one stream without ordering) race
-// on it.  Each call writes every scratch element it later reads, so nothing
-// has to start at zero.
-constexpr size_t kNoAllocScratchBytes = size_t(1) << 20;
-static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads, 1) svd_noalloc_kernel(int m, int n, const cplx<T> *C,
-                                                                  cplx<T> *work, cplx<T> *V, T *sig2) {
-  extern __shared__ __align__(16) char smem_raw[];
-  double *red = reinterpret_cast<double *>(smem_raw);
-  double *dm = red + kThreads;
-  int *flag = reinterpret_cast<int *>(dm + 16);
-  cplx<T> *buf = reinterpret_cast<cplx<T> *>(flag + 16) + kMaxVec;
-  for (int e = tid(); e < m * n; e += kThreads) work[e] = C[e];
-  __syncthreads();
-  // the large-bond path of the truncation sweep on the work copy: R factor,
-  // Jacobi on X = R^dag, V = normalised columns of X
-  qr_r_inplace<T>(m, n, work, n, buf, SvdSmem<T>::elems, red, dm);
-  const int k = min(m, n);
-  const bool x_smem = n * k <= SvdSmem<T>::elems;
-  cplx<T> *Xc = x_smem ? buf : work;
-  for (int e = tid(); e < n * k; e += kThreads) Xc[e] = cconj(work[e]);
-  __syncthreads();
-  if (x_smem) svd_onesided<T>(n, k, Xc, nullptr, sig2, flag, red);
-  else svd_onesided_blocked<T>(n, k, Xc, nullptr, sig2, flag, red, buf, SvdSmem<T>::elems);
-  for (int e = tid(); e < n * n; e += kThreads) {
-    const int c = e / n;
-    const T l = c < k ? sig2[c] : T(0);
-    V[e] = l > T(0) ? cscale(Xc[e], T(1) / sqrt(l)) : cmake<T>(0, 0);
-  }
-  for (int c = k + tid(); c < n; c += kThreads) sig2[c] = T(0);
-}
-
-size_t noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
-
-// Device address of the scratch array on the current device.  Host code may
-// not pass g_noalloc_scratch itself: on the host that name is a stand-in, not
-// a device address.  The address is looked up once per device, with that
-// device current, on the first call made there.
-static cudaError_t noalloc_scratch_ptr(void **out) {
-  constexpr int kMaxDevices = 64;
-  static std::mutex mu;
-  static void *ptr[kMaxDevices] = {};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(mu);
-  if (ptr[dev] == nullptr) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    ptr[dev] = p;
-  }
-  *out = ptr[dev];
-  return cudaSuccess;
-}
-
-template <typename T>
-static cudaError_t launch_svd_noalloc_t(int m, int n, const void *C, void *V, void *sig2, cudaStream_t s) {
-  void *work = nullptr;
-  cudaError_t e = noalloc_scratch_ptr(&work);
-  if (e != cudaSuccess) return e;
-  size_t smem = sizeof(double) * (kThreads + 16) + sizeof(int) * 16 + sizeof(cplx<T>) * kMaxVec +
-                sizeof(cplx<T>) * SvdSmem<T>::elems;
-  e = cudaFuncSetAttribute(svd_noalloc_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
-  svd_noalloc_kernel<T><<<1, kThreads, smem, s>>>(m, n, static_cast<const cplx<T> *>(C),
-                                                  static_cast<cplx<T> *>(work), static_cast<cplx<T> *>(V),
-                                                  static_cast<T *>(sig2));
-  return cudaGetLastError();
-}
-
-cudaError_t launch_svd_noalloc(int precision, int m, int n, const void *C, void *V, void *sig2,
-                               cudaStream_t s) {
-  return precision == 0 ? launch_svd_noalloc_t<double>(m, n, C, V, sig2, s)
-                        : launch_svd_noalloc_t<float>(m, n, C, V, sig2, s);
 }
 
 int svd_smem_elems(int precision) { return precision == 0 ? SvdSmem<double>::elems : SvdSmem<float>::elems; }
@@ -2177,30 +105,20 @@ int jacobi_smem_limit(int precision) {
   return precision == 0 ? SvdSmem<double>::elems : SvdSmem<float>::elems;
 }
 
-template <typename T>
-static cudaError_t launch_init_t(const EngineParams &p, cudaStream_t s) {
-  int grid = p.shots < 4096 ? p.shots : 4096;
-  if (grid < 1) return cudaSuccess;
-  init_kernel<T><<<grid, 128, 0, s>>>(p);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_init(int precision, const EngineParams &p, cudaStream_t s) {
-  return precision == 0 ? launch_init_t<double>(p, s) : launch_init_t<float>(p, s);
+  return precision == 0 ? launch_init_f64(p, s) : launch_init_f32(p, s);
 }
 
-template <typename T>
-static cudaError_t launch_round_t(const EngineParams &p, int grid, cudaStream_t s) {
-  size_t smem = smem_bytes<T>(p.n, p.W, p.svd_elems);
-  cudaError_t e = cudaFuncSetAttribute(round_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
-  round_kernel<T><<<grid, kThreads, smem, s>>>(p);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_round(int precision, const EngineParams &p, int grid, cudaStream_t s) {
-  return precision == 0 ? launch_round_t<double>(p, grid, s) : launch_round_t<float>(p, grid, s);
+  return precision == 0 ? launch_round_f64(p, grid, s) : launch_round_f32(p, grid, s);
+}
+
+cudaError_t launch_dense_check(int precision, int what, int m, int n, void *A, void *V, void *sig2,
+                               int use_smem, cudaStream_t s) {
+  return precision == 0 ? launch_dense_check_f64(what, m, n, A, V, sig2, use_smem, s)
+                        : launch_dense_check_f32(what, m, n, A, V, sig2, use_smem, s);
 }
 
 cudaError_t launch_philox(uint64_t seed, uint64_t shot_offset, int64_t n_shots, uint32_t event_offset,

@@ -65,6 +65,15 @@ int round_kernel_svd_elems(int precision, int n, int W);
 int jacobi_smem_limit(int precision);
 
 cudaError_t launch_init(int precision, const EngineParams &p, cudaStream_t s);
+// per-precision instantiations (engine_f32.cu, engine_f64.cu)
+cudaError_t launch_round_f32(const EngineParams &p, int grid, cudaStream_t s);
+cudaError_t launch_round_f64(const EngineParams &p, int grid, cudaStream_t s);
+cudaError_t launch_init_f32(const EngineParams &p, cudaStream_t s);
+cudaError_t launch_init_f64(const EngineParams &p, cudaStream_t s);
+cudaError_t launch_dense_check_f32(int what, int m, int n, void *A, void *V, void *sig2, int use_smem,
+                                   cudaStream_t s);
+cudaError_t launch_dense_check_f64(int what, int m, int n, void *A, void *V, void *sig2, int use_smem,
+                                   cudaStream_t s);
 cudaError_t launch_round(int precision, const EngineParams &p, int grid, cudaStream_t s);
 cudaError_t launch_dense_check(int precision, int what, int m, int n, void *A, void *V, void *sig2,
                                int use_smem, cudaStream_t s);

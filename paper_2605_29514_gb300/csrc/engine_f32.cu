@@ -1,0 +1,17 @@
+// Complex64 instantiations of the round, init and dense-check kernels.
+#include "engine_kernels.cuh"
+
+namespace stn {
+
+cudaError_t launch_round_f32(const EngineParams &p, int grid, cudaStream_t s) {
+  return launch_round_t<float>(p, grid, s);
+}
+
+cudaError_t launch_init_f32(const EngineParams &p, cudaStream_t s) { return launch_init_t<float>(p, s); }
+
+cudaError_t launch_dense_check_f32(int what, int m, int n, void *A, void *V, void *sig2, int use_smem,
+                                     cudaStream_t s) {
+  return launch_dense_check_t<float>(what, m, n, A, V, sig2, use_smem, s);
+}
+
+}  // namespace stn

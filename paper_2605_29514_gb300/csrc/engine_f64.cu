@@ -1,0 +1,17 @@
+// Complex128 instantiations of the round, init and dense-check kernels.
+#include "engine_kernels.cuh"
+
+namespace stn {
+
+cudaError_t launch_round_f64(const EngineParams &p, int grid, cudaStream_t s) {
+  return launch_round_t<double>(p, grid, s);
+}
+
+cudaError_t launch_init_f64(const EngineParams &p, cudaStream_t s) { return launch_init_t<double>(p, s); }
+
+cudaError_t launch_dense_check_f64(int what, int m, int n, void *A, void *V, void *sig2, int use_smem,
+                                     cudaStream_t s) {
+  return launch_dense_check_t<double>(what, m, n, A, V, sig2, use_smem, s);
+}
+
+}  // namespace stn
