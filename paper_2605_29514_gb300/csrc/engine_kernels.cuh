@@ -1492,65 +1492,6 @@ static __device__ double mps_expect(const EngineParams &P, const Smem<T> &S, int
   }
 }
 
-// The same contraction in double precision from the (single-precision) site
-// tensors, for spans whose bonds are all <= kExpect64Chi: shared-memory
-// buffers only.  Used by the complex64 path so that Born probabilities keep
-// double accuracy where it is cheap.
-constexpr int kExpect64Chi = 32;
-
-template <typename T>
-static __device__ double mps_expect64(const EngineParams &P, const Smem<T> &S, int64_t shot, int a, int b, int m) {
-  const int *chi = S.chi;
-  const int c = kExpect64Chi, c2 = c * c;
-  cplx<double> *E = reinterpret_cast<cplx<double> *>(S.jbuf);
-  cplx<double> *SA = E + c2, *TE = SA + 2 * c2, *AD = TE + 2 * c2;
-  cplx<double> *tile = AD + 2 * c2;
-  const cplx<double> one = cmake<double>(1, 0), zero = cmake<double>(0, 0);
-  MpoSpec<double> sp;
-  sp.kind = MPO_ROT; sp.lo = -1; sp.hi = -1; sp.j = -1;
-  sp.w0 = one; sp.w1 = one; sp.v0 = zero; sp.v1 = zero;
-  for (int k = a; k <= b; ++k) {
-    const cplx<T> *A = site_ptr<T>(P, shot, k);
-    const int cl = chi[k], cr = chi[k + 1];
-    cplx<double> op[4];
-    site_op(sp, S.ppx, S.ppz, k, 1, op);
-    const int tot = cl * 2 * cr;
-    for (int e = tid(); e < tot; e += kThreads) {
-      cplx<T> v = A[e];
-      AD[e] = cmake<double>(static_cast<double>(v.re), static_cast<double>(v.im));
-    }
-    __syncthreads();
-    for (int e = tid(); e < tot; e += kThreads) {
-      int r = e % cr, s = (e / cr) % 2, l = e / (2 * cr);
-      cplx<double> v = cmake<double>(0, 0);
-      cfma(v, op[s * 2 + 0], AD[(l * 2 + 0) * cr + r]);
-      cfma(v, op[s * 2 + 1], AD[(l * 2 + 1) * cr + r]);
-      SA[e] = v;
-    }
-    __syncthreads();
-    if (k == a) {
-      cgemm<double, 1, 0>(cr, cr, 2 * cl, one, AD, cr, SA, cr, zero, E, cr, tile);
-    } else {
-      cgemm<double, 0, 0>(cl, 2 * cr, cl, one, E, cl, SA, 2 * cr, zero, TE, 2 * cr, tile);
-      cgemm<double, 1, 0>(cr, cr, 2 * cl, one, AD, cr, TE, cr, zero, E, cr, tile);
-    }
-  }
-  const int cb = chi[b + 1];
-  double re = 0, im = 0;
-  for (int i = tid(); i < cb; i += kThreads) {
-    re += E[i * cb + i].re;
-    im += E[i * cb + i].im;
-  }
-  re = block_sum(re, S.red);
-  im = block_sum(im, S.red);
-  switch (m & 3) {
-    case 0: return re;
-    case 1: return -im;
-    case 2: return -re;
-    default: return im;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Tableau helpers (shared memory, one thread unless noted).
 static __device__ __forceinline__ int popc64(uint64_t v) { return __popcll(v); }
@@ -1798,36 +1739,20 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
           if (S.misc[M_FAIL]) break;
           int caseB = 0, lidx = 0, outcome = 0;
           if (meas) {
-            // The Born probability of the less likely branch is taken from the
-            // norm of its projected state (accurate for small p); the FP32
+            // The Born probability of the less likely branch is the squared
+            // norm of its projected state, from R factors: any deviation of
+            // the sites outside [a, b] from exact isometries (rounding of the
+            // gauge steps and sweeps) changes it only relatively.  The
             // expectation value only decides which branch that is.
             const int mb = S.misc[M_BIT];
-            bool exact64 = false;
-            if constexpr (sizeof(T) == 4) {
-              constexpr size_t need = sizeof(cplx<double>) * (7 * kExpect64Chi * kExpect64Chi +
-                                                              kBK * (kBM + kPad + kBN + kPad));
-              int mx = 1;
-              for (int k = a; k <= b + 1; ++k) mx = max(mx, S.chi[k]);
-              exact64 = mx <= kExpect64Chi && need <= sizeof(cplx<T>) * static_cast<size_t>(P.svd_elems);
-            }
             long long tq = clock64();
-            double e = 0.0;
-            if constexpr (sizeof(T) == 4) {
-              if (exact64) e = mps_expect64<T>(P, S, shot, a, b, mb & 3);
-              else e = mps_expect<T>(P, S, shot, X, a, b, mb & 3);
-            } else {
-              e = mps_expect<T>(P, S, shot, X, a, b, mb & 3);
-            }
+            const double e = mps_expect<T>(P, S, shot, X, a, b, mb & 3);
             const int small = e >= 0.0 ? 1 : 0;
             if (tid() == 0) set_meas_spec<T>(S, small);
             __syncthreads();
             prof_mark(S.dmisc, PROF_EXPECT, tq);
-            double ps = fmin(1.0, fmax(0.0, mps_prepare<T>(P, S, shot, X, a, b)));
+            const double ps = fmin(1.0, fmax(0.0, mps_prepare<T>(P, S, shot, X, a, b)));
             prof_mark(S.dmisc, PROF_LEFT, tq);
-            // in double precision the expectation value is as accurate as the
-            // projected norm; in single precision it is preferred only where
-            // it was contracted in double
-            if (exact64) ps = fmin(1.0, fmax(0.0, 0.5 * (1.0 - fabs(e))));
             if (tid() == 0) {
               double p0 = small == 0 ? ps : 1.0 - ps;
               double u = philox_uniform(P.seed, gshot, op.ev);
