@@ -708,8 +708,24 @@ static __device__ void svd_onesided_blocked(int m, int n, cplx<T> *C, cplx<T> *V
   const int nb = (n + bw - 1) / bw, nbe = nb + (nb & 1);
   const int max_sweeps = sizeof(T) == 4 ? kMaxBlockedSweepsF : kMaxBlockedSweepsD;
   int *any = flag + 1;
+  // Visits follow a fixed order (each block alone, then the tournament), so
+  // visit v of sweep s has the stamp s * per_sweep + v.  last_mod[I] is the
+  // stamp of the last visit that rotated columns of block I.  A visit whose
+  // previous occurrence (one sweep earlier) rotated nothing, with neither
+  // block changed since, would see the same columns and rotate nothing again:
+  // it is skipped, which changes no result.  The stamps live in `red`, free
+  // between the prologue and the epilogue.
+  const int per_sweep = nb + (nbe - 1) * (nbe / 2);
+  int *last_mod = reinterpret_cast<int *>(red);
+  const bool skipping = nb <= static_cast<int>(kThreads * sizeof(double) / sizeof(int));
+  if (skipping) {
+    for (int i = tid(); i < nb; i += kThreads) last_mod[i] = -1;
+    __syncthreads();
+  }
 
-  auto visit = [&](int I, int J) {
+  auto visit = [&](int I, int J, int stamp) {
+    if (skipping && stamp >= per_sweep && last_mod[I] < stamp - per_sweep && last_mod[J] < stamp - per_sweep)
+      return;
     const bool self = I == J;
     const int c0 = I * bw, wI = min(bw, n - c0);
     const int c1 = J * bw, wJ = self ? 0 : min(bw, n - c1);
@@ -763,6 +779,7 @@ static __device__ void svd_onesided_blocked(int m, int n, cplx<T> *C, cplx<T> *V
     const int rotated = *flag;
     __syncthreads();
     if (!rotated) return;
+    if (skipping && tid() == 0) last_mod[I] = last_mod[J] = stamp;
     for (int e = tid(); e < m * w; e += kThreads) {
       const int c = e / m, i = e % m;
       C[static_cast<int64_t>(gcol(c)) * m + i] = Cb[e];
@@ -802,7 +819,8 @@ static __device__ void svd_onesided_blocked(int m, int n, cplx<T> *C, cplx<T> *V
   for (int sweep = 0; sweep < max_sweeps && n > 1; ++sweep) {
     if (tid() == 0) *any = 0;
     __syncthreads();
-    for (int I = 0; I < nb; ++I) visit(I, I);
+    const int base = sweep * per_sweep;
+    for (int I = 0; I < nb; ++I) visit(I, I, base + I);
     for (int round = 0; round < nbe - 1; ++round) {
       for (int bp = 0; bp < nbe / 2; ++bp) {
         int I, J;
@@ -810,7 +828,7 @@ static __device__ void svd_onesided_blocked(int m, int n, cplx<T> *C, cplx<T> *V
         else { I = (round + bp) % (nbe - 1); J = (round - bp + (nbe - 1)) % (nbe - 1); }
         if (I > J) { int tt = I; I = J; J = tt; }
         if (J >= nb) continue;
-        visit(I, J);
+        visit(I, J, base + nb + round * (nbe / 2) + bp);
       }
     }
     __syncthreads();
