@@ -882,6 +882,7 @@ enum MpoKind { MPO_ROT = 0, MPO_PROJ_Z = 1, MPO_PROJ_B = 2 };
 template <typename T>
 struct MpoSpec {
   int kind, lo, hi, j;
+  int par;         // case A: parity of the Z support that the projector keeps
   cplx<T> w0, w1;  // branch weights (folded into site lo)
   cplx<T> v0, v1;  // measurement eigenvector at site j (case B)
 };
@@ -1059,6 +1060,26 @@ __device__ __forceinline__ cplx<T> *site_ptr(const EngineParams &P, int64_t shot
 template <typename T>
 static __device__ void materialize(const MpoSpec<T> &sp, const uint64_t *ppx, const uint64_t *ppz, int k,
                             const cplx<T> *A, int chl, int chr, bool dl, bool dr, cplx<T> *out) {
+  if (sp.kind == MPO_PROJ_Z) {
+    // (I + s Z_S)/2 written without its two cancelling branches: the bond
+    // index carries the parity of the S bits to the left, a site in S adds
+    // its own bit, and the last site keeps only the target parity.  All
+    // entries are 0 or 1, so a small Born probability is not the difference
+    // of two numbers of order one.
+    const bool in_s = (ppz[k >> 6] >> (k & 63)) & 1;
+    const int Dl = dl ? 2 * chl : chl, Dr = dr ? 2 * chr : chr;
+    const int64_t total = static_cast<int64_t>(Dl) * 2 * Dr;
+    for (int64_t e = tid(); e < total; e += kThreads) {
+      const int R = static_cast<int>(e % Dr);
+      const int sb = static_cast<int>((e / Dr) % 2);
+      const int L = static_cast<int>(e / (2 * Dr));
+      const int al = dl ? L / chl : 0, l = dl ? L % chl : L;
+      const int be = dr ? R / chr : sp.par, r = dr ? R % chr : R;
+      const bool keep = in_s ? ((al ^ sb) == be) : (al == be);
+      out[e] = keep ? A[(static_cast<int64_t>(l) * 2 + sb) * chr + r] : cmake<T>(0, 0);
+    }
+    return;
+  }
   cplx<T> op0[4], op1[4];
   site_op(sp, ppx, ppz, k, 0, op0);
   site_op(sp, ppx, ppz, k, 1, op1);
@@ -1612,11 +1633,13 @@ static __device__ void set_meas_spec(const Smem<T> &S, int bit) {
   const int m = mb & 3;
   const int neg = (mb >> 4) & 1;
   if (!S.misc[M_CASEB]) {
+    // P' = i^m Z^z with m even (Hermitian, no X): keep the states whose S
+    // parity makes (-1)^b i^m (-1)^parity = +1
     sp.kind = MPO_PROJ_Z;
-    sp.w0 = cmake<T>(T(0.5), 0);
-    cplx<T> w1 = ipow<T>(m);
-    T sgn = bit ? T(-0.5) : T(0.5);
-    sp.w1 = cmake<T>(w1.re * sgn, w1.im * sgn);
+    const int sgn = (bit ? -1 : 1) * ((m & 2) ? -1 : 1);
+    sp.par = sgn > 0 ? 0 : 1;
+    sp.w0 = cmake<T>(1, 0);
+    sp.w1 = cmake<T>(1, 0);
   } else {
     const int jq = S.misc[M_J];
     const bool zj = (S.ppz[jq >> 6] >> (jq & 63)) & 1;
