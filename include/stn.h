@@ -224,6 +224,13 @@ stn_status stn_philox_uniforms(uint64_t seed, uint64_t shot_offset, int64_t n_sh
  *   entries are zero.
  * Errors: STN_EINVAL on bad sizes, STN_ECUDA on launch failure. */
 stn_status stn_dense_qr(int32_t precision, int32_t m, int32_t n, void *d_b, void *cuda_stream);
+/* Explicit-Q Householder QR, as the gauge steps that move the orthogonality
+ * centre use it (Sec. IV B): d_b (m x n, row-major, m <= 1024) becomes R as
+ * for stn_dense_qr, d_q (m x min(m,n), row-major) receives Q with A = Q R,
+ * and d_work (m x min(m,n) complex) holds the reflectors.  Errors: STN_EINVAL
+ * on bad sizes, STN_ECUDA on launch failure. */
+stn_status stn_dense_qr_q(int32_t precision, int32_t m, int32_t n, void *d_b, void *d_q, void *d_work,
+                          void *cuda_stream);
 stn_status stn_dense_svd(int32_t precision, int32_t m, int32_t n, void *d_c, void *d_v, void *d_sig2,
                          int32_t in_shared, void *cuda_stream);
 

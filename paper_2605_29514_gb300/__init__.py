@@ -220,6 +220,13 @@ def philox_uniforms(seed, shot_offset, n_shots, event_offset, n_events, d_out_pt
         raise StnError(st, "stn_philox_uniforms failed")
 
 
+def dense_qr_q(precision, m, n, d_b, d_q, d_work, stream=0):
+    st = load().stn_dense_qr_q(int(precision), int(m), int(n), ctypes.c_void_p(d_b), ctypes.c_void_p(d_q),
+                               ctypes.c_void_p(d_work), ctypes.c_void_p(stream))
+    if st != STN_OK:
+        raise StnError(st, "stn_dense_qr_q failed")
+
+
 def dense_qr(precision, m, n, d_b, stream=0):
     st = load().stn_dense_qr(int(precision), int(m), int(n), ctypes.c_void_p(d_b), ctypes.c_void_p(stream))
     if st != STN_OK:

@@ -479,6 +479,15 @@ stn_status stn_logprob_grad(stn_ctx *c, const uint8_t *, int64_t, const double *
   return fail(c, STN_ENOTIMPL, "stn_logprob_grad is not implemented");
 }
 
+stn_status stn_dense_qr_q(int32_t precision, int32_t m, int32_t n, void *d_b, void *d_q, void *d_work,
+                          void *cuda_stream) {
+  if ((precision != 0 && precision != 1) || m < 1 || n < 1 || m > 1024 || !d_b || !d_q || !d_work)
+    return STN_EINVAL;
+  cudaError_t e = stn::launch_dense_check(precision, 2, m, n, d_b, d_q, d_work, 0,
+                                          static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? STN_OK : STN_ECUDA;
+}
+
 stn_status stn_dense_qr(int32_t precision, int32_t m, int32_t n, void *d_b, void *cuda_stream) {
   if ((precision != 0 && precision != 1) || m < 1 || n < 1 || m > 1024 || !d_b) return STN_EINVAL;
   cudaError_t e = stn::launch_dense_check(precision, 0, m, n, d_b, nullptr, nullptr, 0,

@@ -1905,6 +1905,11 @@ __global__ void __launch_bounds__(kThreads, 1) dense_check_kernel(int what, int 
   cplx<T> *buf = uv + kMaxVec;
   if (what == 0) {
     qr_r_inplace<T>(m, n, A, n, buf, SvdSmem<T>::elems, red, dm);
+  } else if (what == 2) {
+    // explicit Q of the gauge steps: reflectors kept in sig2's buffer
+    cplx<T> *vstore = reinterpret_cast<cplx<T> *>(sig2);
+    qr_r_inplace<T>(m, n, A, n, buf, SvdSmem<T>::elems, red, dm, vstore);
+    form_q<T>(m, min(m, n), vstore, V, buf, SvdSmem<T>::elems);
   } else if (use_smem == 3) {
     // the large-bond path of the truncation sweep: A row-major (m x n),
     // R factor, Jacobi on X = R^dag (n x k), V = normalised columns of X

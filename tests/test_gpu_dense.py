@@ -112,3 +112,23 @@ def test_large_bond_svd(precision, m, n, decay):
     q, _ = np.linalg.qr(vk)  # the sweep re-orthonormalises the kept vectors
     err = np.abs(a @ q @ q.conj().T - best).max()
     assert err < TOL[precision] * 10 * s_ref[0], err
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("m,n", [(2, 1), (4, 8), (8, 4), (16, 16), (64, 32), (33, 47), (40, 64), (128, 64),
+                                 (512, 256)])
+def test_explicit_q_factor(precision, m, n):
+    """The gauge step's explicit-Q Householder QR: Q has orthonormal columns
+    and Q R reproduces A."""
+    rng = np.random.default_rng(3 * m + n)
+    a = rand(rng, m, n, decay=0.2)
+    k = min(m, n)
+    db = torch.tensor(a, dtype=CDT[precision], device="cuda")
+    dq = torch.zeros((m, k), dtype=CDT[precision], device="cuda")
+    dw = torch.zeros((m, k), dtype=CDT[precision], device="cuda")
+    stn.dense_qr_q(precision, m, n, db.data_ptr(), dq.data_ptr(), dw.data_ptr())
+    torch.cuda.synchronize()
+    r = db.cpu().numpy().astype(np.complex128)[:k]
+    q = dq.cpu().numpy().astype(np.complex128)
+    assert np.abs(q.conj().T @ q - np.eye(k)).max() < TOL[precision] * 10
+    assert np.abs(q @ r - a).max() < TOL[precision] * 10 * np.abs(a).max()
