@@ -188,6 +188,13 @@ stn_status stn_read_tableau(stn_ctx *ctx, int64_t shot, uint64_t *h_x, uint64_t 
 /* Bond dimensions chi_0..chi_{n-2} of one shot's MPS (synchronises). */
 stn_status stn_read_bonds(stn_ctx *ctx, int64_t shot, int32_t *h_bonds);
 
+/* Site tensor k of one shot's MPS (synchronises): chi_k x 2 x chi_{k+1}
+ * complex elements of the path's precision, row-major, copied to h_site
+ * (caller-owned, sized from stn_read_bonds; chi_0 = chi_n = 1).  With the
+ * tableau this gives the full state |psi> = C |MPS> (Eq. 7) of small cases.
+ * Errors: STN_EINVAL for a bad shot or site. */
+stn_status stn_read_site(stn_ctx *ctx, int64_t shot, int32_t k, void *h_site);
+
 /* Whole job: begin_batch, every segment with h_theta, read_records. */
 stn_status stn_sample_shots(stn_ctx *ctx, int64_t shots, uint64_t shot_offset,
                             const double *h_theta, uint8_t *h_records, double *h_born,

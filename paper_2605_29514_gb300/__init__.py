@@ -158,6 +158,17 @@ class Simulator:
         self._check(self.lib.stn_read_bonds(self.ctx, int(shot), _ptr(b)))
         return b
 
+    def read_mps(self, shot):
+        """Site tensors of one shot's MPS as complex numpy arrays (chi_k, 2, chi_k+1)."""
+        bonds = [1] + list(self.read_bonds(shot)) + [1]
+        dt = np.complex128 if self.cfg.precision == 0 else np.complex64
+        sites = []
+        for k in range(self.n_qubits):
+            a = np.zeros((bonds[k], 2, bonds[k + 1]), dtype=dt)
+            self._check(self.lib.stn_read_site(self.ctx, int(shot), int(k), _ptr(a)))
+            sites.append(a)
+        return sites
+
     def sample_shots(self, shots, shot_offset, theta, born=True, stats=True):
         theta = np.ascontiguousarray(theta, dtype=np.float64)
         self.begin_batch(shots, shot_offset)

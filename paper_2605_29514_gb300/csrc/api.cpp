@@ -466,6 +466,22 @@ stn_status stn_read_bonds(stn_ctx *c, int64_t shot, int32_t *h_bonds) {
   return STN_OK;
 }
 
+stn_status stn_read_site(stn_ctx *c, int64_t shot, int32_t k, void *h_site) {
+  if (!c || shot < 0 || shot >= c->shots || k < 0 || k >= c->n || !h_site)
+    return fail(c, STN_EINVAL, "bad argument");
+  stn_status st = stn_sync(c);
+  if (st != STN_OK) return st;
+  int dims[2];
+  cudaError_t e = cudaMemcpy(dims, c->d_chi + shot * (c->n + 1) + k, sizeof(int) * 2, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) {
+    const size_t bytes = c->elem * 2ull * dims[0] * dims[1];
+    const char *src = static_cast<const char *>(c->d_mps) + c->elem * (shot * c->slab_elems + c->site_off[k]);
+    e = cudaMemcpy(h_site, src, bytes, cudaMemcpyDeviceToHost);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "stn_read_site");
+  return STN_OK;
+}
+
 stn_status stn_sample_shots(stn_ctx *c, int64_t shots, uint64_t shot_offset, const double *h_theta,
                             uint8_t *h_records, double *h_born, stn_shot_stats *h_stats) {
   stn_status st = stn_begin_batch(c, shots, shot_offset);
