@@ -72,6 +72,14 @@ template <typename T>
 __device__ __forceinline__ T cabs2(cplx<T> a) {
   return a.re * a.re + a.im * a.im;
 }
+// |a|^2 in double from double components: in single precision the square of
+// a component below about 1e-19 is a denormal or zero, which would make the
+// norm of a tiny vector (and a reflector built from it) inaccurate.
+template <typename T>
+__device__ __forceinline__ double cabs2d(cplx<T> a) {
+  const double re = static_cast<double>(a.re), im = static_cast<double>(a.im);
+  return re * re + im * im;
+}
 // i^m
 template <typename T>
 __device__ __forceinline__ cplx<T> ipow(int m) {
@@ -304,11 +312,11 @@ static __device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *p
     __syncthreads();
     for (int jj = 0; jj < jb; ++jj) {
       double nx2 = 0;
-      for (int i = jj + tid(); i < mr; i += kThreads) nx2 += static_cast<double>(cabs2(Vp[i * nb + jj]));
+      for (int i = jj + tid(); i < mr; i += kThreads) nx2 += cabs2d(Vp[i * nb + jj]);
       nx2 = block_sum(nx2, red);
       // rows above the diagonal of this column are final R entries
       for (int i = tid(); i < jj; i += kThreads) B[static_cast<int64_t>(j0 + i) * ld + j0 + jj] = Vp[i * nb + jj];
-      if (!(nx2 > 0.0)) {  // zero column: no reflector, R row jj is final
+      if (!(nx2 > 1e-60)) {  // (numerically) zero column: no reflector, R row jj is final
         for (int i = tid(); i < mr; i += kThreads) {
           if (i >= jj) B[static_cast<int64_t>(j0 + i) * ld + j0 + jj] = cmake<T>(0, 0);
           Vp[i * nb + jj] = cmake<T>(0, 0);
@@ -318,7 +326,7 @@ static __device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *p
       }
       if (tid() == 0) {
         cplx<T> al = Vp[jj * nb + jj];
-        double aa = sqrt(static_cast<double>(cabs2(al)));
+        double aa = sqrt(cabs2d(al));
         double nx = sqrt(nx2);
         double pr = aa > 0 ? al.re / aa : 1.0, pi = aa > 0 ? al.im / aa : 0.0;
         dm[0] = -pr * nx;  // gamma
@@ -582,7 +590,7 @@ static __device__ T onesided_prologue(int m, int n, const cplx<T> *C, cplx<T> *V
     V[e] = cmake<T>(i == j ? T(1) : T(0), 0);
   }
   double fro2 = 0;
-  for (int64_t e = tid(); e < static_cast<int64_t>(m) * n; e += kThreads) fro2 += static_cast<double>(cabs2(C[e]));
+  for (int64_t e = tid(); e < static_cast<int64_t>(m) * n; e += kThreads) fro2 += cabs2d(C[e]);
   fro2 = block_sum(fro2, red);
   return static_cast<T>(static_cast<double>(Eps<T>::v) * static_cast<double>(Eps<T>::v) * fro2);
 }
@@ -591,7 +599,7 @@ template <typename T>
 static __device__ void onesided_epilogue(int m, int n, const cplx<T> *C, T *sig2) {
   for (int j = warp_id(); j < n; j += kWarps) {
     double a = 0;
-    for (int i = lane_id(); i < m; i += 32) a += static_cast<double>(cabs2(C[static_cast<int64_t>(j) * m + i]));
+    for (int i = lane_id(); i < m; i += 32) a += cabs2d(C[static_cast<int64_t>(j) * m + i]);
     a = warp_sum(a);
     if (lane_id() == 0) sig2[j] = static_cast<T>(a);
   }
@@ -1223,7 +1231,7 @@ static __device__ double mps_prepare(const EngineParams &P, const Smem<T> &S, in
     __syncthreads();
     const int64_t tot = static_cast<int64_t>(chi[a]) * 2 * chi[a + 1];
     double nrm = 0;
-    for (int64_t e = tid(); e < tot; e += kThreads) nrm += static_cast<double>(cabs2(X.t[e]));
+    for (int64_t e = tid(); e < tot; e += kThreads) nrm += cabs2d(X.t[e]);
     return block_sum(nrm, S.red);
   }
   // doubled bond dimensions D[k] for bonds a..b+1
@@ -1297,7 +1305,7 @@ static __device__ double mps_prepare(const EngineParams &P, const Smem<T> &S, in
     const int Dl = Dbond(b), n2 = 2 * Dbond(b + 1), r = S.rdim[b - a];
     cgemm<T, 0, 0>(r, n2, Dl, one, X.g + S.goff[b - a], Dl, X.ap + S.off[b - a], n2, zero, X.y, n2, S.tile);
     double nrm = 0;
-    for (int e = tid(); e < r * n2; e += kThreads) nrm += static_cast<double>(cabs2(X.y[e]));
+    for (int e = tid(); e < r * n2; e += kThreads) nrm += cabs2d(X.y[e]);
     return block_sum(nrm, S.red);
   }
 }
@@ -1313,7 +1321,7 @@ static __device__ void mps_finish(const EngineParams &P, const Smem<T> &S, int64
     cplx<T> *A = site_ptr<T>(P, shot, a);
     const int64_t tot = static_cast<int64_t>(chi[a]) * 2 * chi[a + 1];
     double nrm = 0;
-    for (int64_t e = tid(); e < tot; e += kThreads) nrm += static_cast<double>(cabs2(X.t[e]));
+    for (int64_t e = tid(); e < tot; e += kThreads) nrm += cabs2d(X.t[e]);
     nrm = block_sum(nrm, S.red);
     T inv = static_cast<T>(nrm > 0 ? 1.0 / sqrt(nrm) : 0.0);
     for (int64_t e = tid(); e < tot; e += kThreads) A[e] = cscale(X.t[e], inv);
@@ -1465,7 +1473,7 @@ static __device__ void mps_finish(const EngineParams &P, const Smem<T> &S, int64
   cplx<T> *Aa = site_ptr<T>(P, shot, a);
   const int64_t tot = static_cast<int64_t>(chi[a]) * 2 * kappa;
   double nrm = 0;
-  for (int64_t e = tid(); e < tot; e += kThreads) nrm += static_cast<double>(cabs2(M[e]));
+  for (int64_t e = tid(); e < tot; e += kThreads) nrm += cabs2d(M[e]);
   nrm = block_sum(nrm, S.red);
   T inv = static_cast<T>(nrm > 0 ? 1.0 / sqrt(nrm) : 0.0);
   for (int64_t e = tid(); e < tot; e += kThreads) Aa[e] = cscale(M[e], inv);
