@@ -192,3 +192,38 @@ def test_detectors_and_logical_on_device():
             assert list(det[s]) == detectors(prog, rec)
             assert int(obs[s]) == logical_z(prog, rec)
         sim.close()
+
+
+def test_complex64_strong_rotation_parity():
+    """theta = 0.2 on the d=3 circuit in complex64: rotations of this size
+    leave FP32 noise entries of order 1e-20 in projected states, whose squares
+    are single-precision denormals.  The Householder steps must stay unitary
+    regardless (Born within 1e-5 of the oracle)."""
+    w = D3_EXACT.with_(precision=PRECISION_C64, svd_cutoff=D5_BENCH.svd_cutoff,
+                       degeneracy_tol=D5_BENCH.degeneracy_tol, theta=0.2, rounds=2)
+    shots = 8
+    sim, out, theta = gpu_run(w, shots)
+    prog = make_program(w)
+    for s in range(shots):
+        ref = run_shot(w, s, theta, prog)
+        compare_shot(sim, out, s, ref, 1e-5, check_tableau=False)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mps_stays_canonical(precision):
+    """After whole syndrome rounds every site left of the orthogonality centre
+    is a left isometry and every site right of it a right isometry (the gauge
+    steps and sweeps of Sec. IV B preserve the mixed canonical form), and the
+    state has unit norm."""
+    tol = 1e-12 if precision == 0 else 2e-5
+    w = D3_EXACT.with_(precision=precision, svd_cutoff=5e-6, degeneracy_tol=5e-6, theta=0.2, p=0.01)
+    sim, out, _ = gpu_run(w, 4)
+    for s in range(4):
+        sites = [a.astype(np.complex128) for a in sim.read_mps(s)]
+        left = [np.abs(a.reshape(-1, a.shape[2]).conj().T @ a.reshape(-1, a.shape[2]) - np.eye(a.shape[2])).max()
+                for a in sites]
+        right = [np.abs(a.reshape(a.shape[0], -1) @ a.reshape(a.shape[0], -1).conj().T - np.eye(a.shape[0])).max()
+                 for a in sites]
+        c = next((k for k in range(len(sites)) if left[k] > tol), len(sites) - 1)
+        assert max(right[c + 1:], default=0.0) < tol, f"shot {s}: right-canonical part broken"
+        assert abs(np.sum(np.abs(sites[c]) ** 2) - 1.0) < 10 * tol, f"shot {s}: norm"
