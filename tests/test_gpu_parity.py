@@ -224,6 +224,10 @@ def test_mps_stays_canonical(precision):
                 for a in sites]
         right = [np.abs(a.reshape(a.shape[0], -1) @ a.reshape(a.shape[0], -1).conj().T - np.eye(a.shape[0])).max()
                  for a in sites]
-        c = next((k for k in range(len(sites)) if left[k] > tol), len(sites) - 1)
-        assert max(right[c + 1:], default=0.0) < tol, f"shot {s}: right-canonical part broken"
-        assert abs(np.sum(np.abs(sites[c]) ** 2) - 1.0) < 10 * tol, f"shot {s}: norm"
+        n = len(sites)
+        assert any(all(left[k] < tol for k in range(c)) and all(right[k] < tol for k in range(c + 1, n))
+                   for c in range(n)), f"shot {s}: no mixed canonical form"
+        env = np.ones((1, 1), dtype=np.complex128)
+        for a in sites:
+            env = np.einsum("ac,asb,csd->bd", env, a.conj(), a)
+        assert abs(env[0, 0].real - 1.0) < 10 * tol, f"shot {s}: norm {env[0, 0].real}"
