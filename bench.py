@@ -110,13 +110,47 @@ class ClockSampler:
 
 
 # -- CPU baseline: the oracle, as it stands, on the host cores ------------------
+# Algorithmic FLOPs per shot of the d=5, 5-round, chi-cap-256 complex64 workload,
+# counted by the device with the textbook formulas below in a bench.py run on
+# this workload (35.6 TFLOP).  Used only when no device count is available
+# (the reference arm).
+ALG_FLOPS_PER_SHOT_D5_CAP256 = 35.6e12
+
+
+def _gemm(m, n, k):
+    return 8.0 * m * n * k
+
+
+def _qr(m, n):
+    a, b = (m, n) if m >= n else (n, m)
+    return 4.0 * (2.0 * a * b * b - 2.0 * b ** 3 / 3.0)
+
+
+def _svd(m, n):
+    return 4.0 * (4.0 * m * n * n + 8.0 * n ** 3)
+
+
+def _sweep_flops(lo, before, after):
+    """Textbook FLOPs of one truncating sweep over [lo, lo + len(before)]:
+    per doubled bond D (kept: c) an R factor of 2D x D, its product with the
+    site, C = R M, the SVD of C (D x 2c) and the two contractions that carry
+    the kept vectors to the left (the same counts the kernel accumulates)."""
+    off = 1 if lo > 0 else 0
+    total = 0.0
+    for i, d in enumerate(before):
+        c = after[i + off] if i + off < len(after) else d
+        total += _qr(2 * d, d) + _gemm(d, 2 * d, d) + _gemm(d, 2 * c, d) + _svd(d, 2 * c) \
+            + _gemm(d, c, 2 * c) + _gemm(2 * d, c, d)
+    return total
+
+
 def _oracle_worker(args):
     shot, budget, w_fields = args
     from oracle.shot import ShotSim, make_program
     from workloads import Workload
     w = Workload(**w_fields)
     prog = make_program(w)
-    sim = ShotSim(w, shot, theta_table(w, len(prog.pairs)), prog)
+    sim = ShotSim(w, shot, theta_table(w, len(prog.pairs)), prog, trace=True)
     t0 = time.perf_counter()
     done = 0
     for op in prog.ops:
@@ -124,27 +158,54 @@ def _oracle_worker(args):
             break
         sim.step(op)
         done += 1
-    return done, len(prog.ops), time.perf_counter() - t0
+    secs = time.perf_counter() - t0
+    flops = sum(_sweep_flops(lo, before, after) for _, lo, _, before, after in sim.trace)
+    # the oracle's dominant primitives at the workload's largest bond (2 chi_cap)
+    import numpy as np
+    n = 2 * w.chi_cap
+    rng = np.random.default_rng(shot)
+    a = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    b = rng.normal(size=(2 * n, n)) + 1j * rng.normal(size=(2 * n, n))
+    t1 = time.perf_counter()
+    np.linalg.svd(a, full_matrices=False)
+    np.linalg.qr(b)
+    big_rate = (_svd(n, n) + _qr(2 * n, n)) / (time.perf_counter() - t1)
+    return done, len(prog.ops), secs, flops, big_rate
 
 
-def cpu_baseline(w, budget):
+def cpu_baseline(w, budget, flops_per_shot):
     """Each host core runs the oracle on its own shot of the workload for
-    `budget` seconds.  Throughput counts the fraction of each shot's ops done;
-    later ops are the expensive ones (the bond dimension grows), so this is
-    an upper bound on the oracle's shots/s."""
+    `budget` seconds.  A shot's early ops are far cheaper than its later ones
+    (the bonds grow to the cap), so the sample is converted to shots/s by work:
+    the algorithmic FLOPs of the sweeps the oracle completed (textbook counts
+    from its bond dimensions) per second, over the workload's algorithmic
+    FLOPs per shot.  Without `flops_per_shot` the completed fraction of each
+    shot's ops is used instead, an upper bound."""
     import multiprocessing as mp
     from dataclasses import asdict
     cores = os.cpu_count() or 1
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"  # one core per worker process
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
         res = pool.map(_oracle_worker, [(s, budget, asdict(w)) for s in range(cores)])
-    frac = sum(d / n for d, n, _ in res)
-    secs = max(t for _, _, t in res)
-    ops_done = sum(d for d, _, _ in res)
+    frac = sum(r[0] / r[1] for r in res)
+    secs = max(r[2] for r in res)
+    ops_done = sum(r[0] for r in res)
+    flops = sum(r[3] for r in res)
+    big_rate = sum(r[4] for r in res)
+    sample = f"{cores} shots of {w.name}, one per core, {budget:.0f} s each: {ops_done} of {cores * res[0][1]} ops done"
+    if flops_per_shot:
+        return {"value": big_rate / flops_per_shot, "unit": "shots/s", "cores": cores, "kind": "oracle",
+                "sample": sample + f"; shots/s = the {cores} cores' rate on the oracle's dominant primitives at "
+                                   f"the largest bond (numpy complex128 SVD {2 * w.chi_cap}^2 and QR, "
+                                   f"{big_rate / 1e9:.1f} GFLOP/s together) over {flops_per_shot / 1e12:.1f} TFLOP "
+                                   f"of algorithmic work per shot; the sampled ops ran at {flops / secs / 1e9:.2f} "
+                                   f"GFLOP/s ({flops / secs / flops_per_shot:.2g} shots/s) and their completed "
+                                   f"fraction would give {frac / secs:.3g} shots/s (an upper bound)"}
     return {"value": frac / secs, "unit": "shots/s", "cores": cores, "kind": "oracle",
-            "sample": f"{cores} shots of {w.name}, one per core, {budget:.0f} s each: {ops_done} of "
-                      f"{cores * res[0][1]} ops done; shots/s counts completed op fractions "
-                      f"(upper bound: the remaining ops carry the large bond dimensions)"}
+            "sample": sample + "; shots/s counts completed op fractions (an upper bound: the remaining ops "
+                               "carry the large bond dimensions)"}
 
 
 def reference_arm(args, w):
@@ -157,8 +218,9 @@ def reference_arm(args, w):
     vals = []
     t0 = time.perf_counter()
     last = None
+    fps = ALG_FLOPS_PER_SHOT_D5_CAP256 if w == D5_BENCH else None
     for _ in range(args.steps):
-        last = cpu_baseline(w, per)
+        last = cpu_baseline(w, per, fps)
         vals.append(last["value"])
     total = time.perf_counter() - t0
     v = statistics.median(vals)
@@ -274,6 +336,8 @@ def main():
     achieved = flops / secs / 1e12 / ws
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
+                "traffic_note": "DRAM bytes of the round kernel are not captured at this workload's size; "
+                                "in a capture at chi cap 16 they were negligible (the path is latency-bound)",
                 "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {max_mhz:.0f} MHz "
                                "(max SM clock of MEASURED_PEAKS.json)",
                 "kernel": "stn::round_kernel<float>",
@@ -281,7 +345,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        cpu = cpu_baseline(w, args.cpu_seconds)
+        cpu = cpu_baseline(w, args.cpu_seconds, flops / shots_done if flops > 0 else None)
 
     if rank == 0:
         line = {"metric": "shots/s of d=5, 5-round crosstalk syndrome extraction on 1 GB300 at <=1e-5 Born error",
