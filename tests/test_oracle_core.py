@@ -242,3 +242,32 @@ def test_oracle_matches_its_stored_records():
         res = run_shot(w, s, theta, prog)
         assert "".join(str(b) for b in res.record) == bits
         assert np.abs(np.array(res.born) - born).max() < 1e-13
+
+
+def test_gauge_moves_are_exact_and_canonical():
+    """The QR gauge steps that move the orthogonality centre into an
+    operator's support (Sec. IV B sweep, reading R7) leave the state unchanged
+    and every site left of the centre a left isometry, every site right of it
+    a right isometry."""
+    rng = np.random.default_rng(5)
+    n = 6
+    m = MPS(n)
+    # entangle with a few random two-branch operators, compressing exactly
+    for lo, hi in [(0, 3), (2, 5), (1, 4), (0, 5)]:
+        m.move_center_into(lo, hi)
+        ops1 = {k: (rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))) for k in range(lo, hi + 1)}
+        m.apply_two_branch(lo, hi, {}, ops1, 0.8, 0.6j)
+        m.compress(lo, hi, chi_cap=64, cutoff=0.0, delta=0.0)
+    psi = m.amplitudes()
+    for target in [5, 0, 3, 1, 4, 2]:
+        m.move_center(target)
+        assert m.center == target
+        assert np.abs(m.amplitudes() - psi).max() < 1e-12
+        for k, a in enumerate(m.A):
+            l, _, r = a.shape
+            if k < target:
+                mat = a.reshape(l * 2, r)
+                assert np.abs(mat.conj().T @ mat - np.eye(r)).max() < 1e-12
+            elif k > target:
+                mat = a.reshape(l, 2 * r)
+                assert np.abs(mat @ mat.conj().T - np.eye(l)).max() < 1e-12
