@@ -2,19 +2,26 @@
 on one GB300 (theta = 0.10 ZZ on idle adjacent pairs, depolarising p = 1e-3
 with the Table I ratios, chi cap 256, complex64 contractions).
 
-A step is one program segment (one syndrome round, or the final readout)
-applied to a batch of B shots; a batch completes after rounds + 1 = 6 steps
-and the next batch starts with new shot indices.  K is rounded up to a
-multiple of 6 so every segment is timed equally often, and
-    value = B * K / 6 / device seconds
-is whole-shot throughput, timed with CUDA events on the simulator's stream;
-the angle table and program are resident in HBM.  The W warm-up steps are
-syndrome round 0 of W fresh batches.  `e2e` is the same batches timed on the
-host clock through the C ABI with host buffers: the angle upload from pinned
-memory and every batch's record download are inside it.
+A step is one program segment (a syndrome round, or the final data readout)
+applied to a batch of B shots, one launch of the persistent round kernel; a
+batch is complete after rounds + 1 = 6 steps and the next batch starts with
+new global shot indices.  Exactly K steps are timed, starting with segment 0
+of a fresh batch, and
+
+    value = shots of the batches completed in the timed region / seconds
+
+(CUDA events on the simulator's stream, angles and program resident in HBM).
+The steps of a batch left incomplete at the end of the timed region are
+timed but their shots are not counted, so the value is conservative.  The W
+warm-up steps are syndrome round 0 of W fresh batches.  `e2e` is the same
+steps timed on the host clock through the C ABI with host buffers: the angle
+upload from pinned memory and every completed batch's record download into
+pinned memory are inside it.
 
 Run: python bench.py [--gpus N] [--steps K] [--warmup W] [--shots B]
-     python bench.py --impl reference    (the CPU oracle on a bounded sample)
+     python bench.py --impl reference      (the CPU oracle, bounded sample)
+     python bench.py --dense-routines      (single-CTA timing of the dense
+                                            routines of the truncation sweep)
 Under torchrun each rank simulates its own disjoint shot range (weak scaling,
 no data-path collective); the slowest rank's time is reported.
 """
@@ -31,25 +38,28 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import D5_BENCH, theta_table  # noqa: E402
+from workloads import D5_BENCH, PRECISION_C128, theta_table  # noqa: E402
 
-PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-SMS = 152
-FP32_LANES_PER_SM = 128
+METRIC = "shots/s of d=5, 5-round crosstalk syndrome extraction on 1 GB300 at <=1e-5 Born error"
+GOLDEN_D5 = os.path.join(ROOT, "tests", "golden", "oracle_d5_records.txt")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=6)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--shots", type=int, default=152, help="shots per batch and rank")
+    ap.add_argument("--shots", type=int, default=0, help="shots per batch and rank (default: one per SM)")
     ap.add_argument("--impl", default="stn", choices=["stn", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget per core")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chi-cap", type=int, default=None,
                     help="override the bond cap (smaller profiling captures only; not a bench line)")
-    return ap.parse_args()
+    ap.add_argument("--precision", default="c64", choices=["c64", "c128"],
+                    help="c128: the plain per-shot complex128 GPU path on the same workload (comparator)")
+    ap.add_argument("--dense-routines", action="store_true",
+                    help="time the truncation sweep's dense routines alone on one CTA and exit")
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -57,6 +67,13 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def timed_plan(steps, segs):
+    """(batch, segment) of each of the `steps` timed steps, and the number of
+    batches the timed region completes."""
+    plan = [divmod(i, segs) for i in range(steps)]
+    return plan, steps // segs
 
 
 # -- clocks during the timed region --------------------------------------------
@@ -109,14 +126,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# -- CPU baseline: the oracle, as it stands, on the host cores ------------------
-# Algorithmic FLOPs per shot of the d=5, 5-round, chi-cap-256 complex64 workload,
-# counted by the device with the textbook formulas below in a bench.py run on
-# this workload (35.6 TFLOP).  Used only when no device count is available
-# (the reference arm).
-ALG_FLOPS_PER_SHOT_D5_CAP256 = 35.6e12
-
-
+# -- textbook FLOP counts (the same formulas the kernel accumulates) ------------
 def _gemm(m, n, k):
     return 8.0 * m * n * k
 
@@ -127,7 +137,8 @@ def _qr(m, n):
 
 
 def _svd(m, n):
-    return 4.0 * (4.0 * m * n * n + 8.0 * n ** 3)
+    a, b = (m, n) if m >= n else (n, m)
+    return 4.0 * (4.0 * a * b * b + 8.0 * b ** 3)
 
 
 def _sweep_flops(lo, before, after):
@@ -144,6 +155,7 @@ def _sweep_flops(lo, before, after):
     return total
 
 
+# -- CPU baseline: the oracle, as it stands, on the host cores ------------------
 def _oracle_worker(args):
     shot, budget, w_fields = args
     from oracle.shot import ShotSim, make_program
@@ -160,27 +172,30 @@ def _oracle_worker(args):
         done += 1
     secs = time.perf_counter() - t0
     flops = sum(_sweep_flops(lo, before, after) for _, lo, _, before, after in sim.trace)
-    # the oracle's dominant primitives at the workload's largest bond (2 chi_cap)
-    import numpy as np
-    n = 2 * w.chi_cap
-    rng = np.random.default_rng(shot)
-    a = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
-    b = rng.normal(size=(2 * n, n)) + 1j * rng.normal(size=(2 * n, n))
-    t1 = time.perf_counter()
-    np.linalg.svd(a, full_matrices=False)
-    np.linalg.qr(b)
-    big_rate = (_svd(n, n) + _qr(2 * n, n)) / (time.perf_counter() - t1)
-    return done, len(prog.ops), secs, flops, big_rate
+    return done, len(prog.ops), secs, flops
+
+
+def golden_whole_shot_seconds():
+    """Whole-shot oracle times recorded by tests/golden/make_oracle_d5_golden.py
+    (one shot per core of the machine that wrote the file), or []."""
+    out = []
+    if os.path.exists(GOLDEN_D5):
+        for line in open(GOLDEN_D5):
+            if line.startswith("# shot") and "oracle_seconds" in line:
+                out.append(float(line.split("oracle_seconds")[1].split()[0]))
+    return out
 
 
 def cpu_baseline(w, budget, flops_per_shot):
-    """Each host core runs the oracle on its own shot of the workload for
-    `budget` seconds.  A shot's early ops are far cheaper than its later ones
-    (the bonds grow to the cap), so the sample is converted to shots/s by work:
-    the algorithmic FLOPs of the sweeps the oracle completed (textbook counts
-    from its bond dimensions) per second, over the workload's algorithmic
-    FLOPs per shot.  Without `flops_per_shot` the completed fraction of each
-    shot's ops is used instead, an upper bound."""
+    """Every host core runs the oracle on its own shot of the workload for
+    `budget` seconds (one BLAS thread each).  The sample is converted to
+    shots/s by work: the algorithmic FLOPs of the sweeps the oracle completed
+    (textbook counts from its bond dimensions), per second of all cores, over
+    the workload's algorithmic FLOPs per shot as the device counted them in
+    this run.  A shot's early ops have small bonds, on which the oracle's
+    numpy calls reach a lower FLOP rate than on the later large ones, so the
+    figure is below what whole shots would give; the whole-shot times
+    recorded with the golden records are quoted beside it."""
     import multiprocessing as mp
     from dataclasses import asdict
     cores = os.cpu_count() or 1
@@ -189,23 +204,25 @@ def cpu_baseline(w, budget, flops_per_shot):
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
         res = pool.map(_oracle_worker, [(s, budget, asdict(w)) for s in range(cores)])
-    frac = sum(r[0] / r[1] for r in res)
     secs = max(r[2] for r in res)
     ops_done = sum(r[0] for r in res)
     flops = sum(r[3] for r in res)
-    big_rate = sum(r[4] for r in res)
-    sample = f"{cores} shots of {w.name}, one per core, {budget:.0f} s each: {ops_done} of {cores * res[0][1]} ops done"
-    if flops_per_shot:
-        return {"value": big_rate / flops_per_shot, "unit": "shots/s", "cores": cores, "kind": "oracle",
-                "sample": sample + f"; shots/s = the {cores} cores' rate on the oracle's dominant primitives at "
-                                   f"the largest bond (numpy complex128 SVD {2 * w.chi_cap}^2 and QR, "
-                                   f"{big_rate / 1e9:.1f} GFLOP/s together) over {flops_per_shot / 1e12:.1f} TFLOP "
-                                   f"of algorithmic work per shot; the sampled ops ran at {flops / secs / 1e9:.2f} "
-                                   f"GFLOP/s ({flops / secs / flops_per_shot:.2g} shots/s) and their completed "
-                                   f"fraction would give {frac / secs:.3g} shots/s (an upper bound)"}
-    return {"value": frac / secs, "unit": "shots/s", "cores": cores, "kind": "oracle",
-            "sample": sample + "; shots/s counts completed op fractions (an upper bound: the remaining ops "
-                               "carry the large bond dimensions)"}
+    rate = flops / secs
+    sample = (f"{cores} shots of {w.name}, one per core, {budget:.0f} s each: {ops_done} of "
+              f"{cores * res[0][1]} ops done at {rate / 1e9:.2f} GFLOP/s of algorithmic work (all cores); "
+              f"shots/s = that rate over {flops_per_shot / 1e12:.2f} TFLOP per shot (device count)")
+    whole = golden_whole_shot_seconds()
+    if whole and w == D5_BENCH:
+        sample += (f"; cross-check: whole shots of this workload took {statistics.median(whole):.0f} s each on one "
+                   f"core of the build machine (tests/golden/make_oracle_d5_golden.py), i.e. "
+                   f"{cores / statistics.median(whole):.3g} shots/s on {cores} such cores")
+    return {"value": rate / flops_per_shot, "unit": "shots/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+
+# Algorithmic FLOPs per shot of the workload as the device counted them (a
+# bench.py run on one GB300, profiles/bench_d5_chi256.md); the reference arm
+# has no device to count them.
+ALG_FLOPS_PER_SHOT_D5_CAP256 = 35.6e12
 
 
 def reference_arm(args, w):
@@ -213,26 +230,103 @@ def reference_arm(args, w):
     if rank != 0:
         return
     per = max(args.cpu_seconds / max(args.steps, 1), 2.0)
-    for _ in range(args.warmup):
-        pass  # the oracle has nothing to warm up; steps below are all timed
     vals = []
     t0 = time.perf_counter()
     last = None
-    fps = ALG_FLOPS_PER_SHOT_D5_CAP256 if w == D5_BENCH else None
     for _ in range(args.steps):
-        last = cpu_baseline(w, per, fps)
+        last = cpu_baseline(w, per, ALG_FLOPS_PER_SHOT_D5_CAP256)
         vals.append(last["value"])
     total = time.perf_counter() - t0
     v = statistics.median(vals)
-    line = {"metric": "shots/s of d=5, 5-round crosstalk syndrome extraction on 1 GB300 at <=1e-5 Born error",
-            "impl": "reference", "value": v, "unit": "shots/s", "n_gpus": ws, "steps": args.steps,
+    line = {"metric": METRIC, "impl": "reference", "value": v, "unit": "shots/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * total / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": {"workload": w.name, "shots_per_batch": last["cores"]},
+            "data": "synthetic", "config": {"workload": w.name, "shots_per_step": last["cores"]},
             "cpu_baseline": {"value": v, "unit": "shots/s", "cores": last["cores"], "kind": "oracle",
                              "sample": last["sample"]},
             "e2e": {"value": v, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# -- arithmetic peaks, measured in this run --------------------------------------
+def measure_peaks(stn, torch, stream):
+    """FP32 FMA, FP64 FMA and TF32 mma.sync rates of this GPU (own probe
+    kernels, CUDA events, best of 3 launches of about 0.1 s)."""
+    names = {0: "fp32_fma", 1: "fp64_fma", 2: "tf32_mma_sync"}
+    iters = {0: 100000, 1: 1500, 2: 50000}
+    out = {}
+    for kind in (0, 1, 2):
+        stn.peak_probe(kind, max(1, iters[kind] // 50), stream.cuda_stream)
+        best = 0.0
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fl = stn.peak_probe(kind, iters[kind], stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            best = max(best, fl / (e0.elapsed_time(e1) / 1e3) / 1e12)
+        out[names[kind]] = best
+    return out
+
+
+# -- single-CTA timing of the dense routines -------------------------------------
+DENSE_SVD_CASES = [(0, 1, 32, 64), (0, 1, 64, 64), (1, 1, 64, 64), (1, 1, 100, 100), (1, 3, 128, 128),
+                   (1, 3, 256, 256), (1, 3, 512, 512), (0, 3, 128, 128), (1, 2, 128, 128)]
+DENSE_QR_CASES = [(1, 256, 128), (1, 1024, 512), (1, 512, 256), (0, 256, 128)]
+
+
+def dense_routines():
+    """The Householder R factor and the one-sided Jacobi SVD variants of the
+    truncation sweep (Sec. IV B) alone on one CTA, at sizes the sweep meets,
+    on graded complex matrices (singular values exp(-0.05 i)); CUDA-event
+    mean of 5 runs after one warm-up.  One JSON line per case."""
+    import numpy as np
+    import torch
+    import paper_2605_29514_gb300 as stn
+    stn.build()
+    cdt = {0: torch.complex128, 1: torch.complex64}
+    rdt = {0: torch.float64, 1: torch.float32}
+
+    def graded(m, n):
+        rng = np.random.default_rng(0)
+        a = rng.normal(size=(m, n)) + 1j * rng.normal(size=(m, n))
+        u, _, vh = np.linalg.svd(a, full_matrices=False)
+        return (u * np.exp(-0.05 * np.arange(min(m, n)))) @ vh
+
+    def timeit(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for prec, mode, m, n in DENSE_SVD_CASES:
+        a = graded(m, n)
+        src = torch.tensor(a if mode == 3 else a.T.copy(), dtype=cdt[prec], device="cuda")
+        dc = src.clone()
+        dv = torch.zeros((n, n), dtype=cdt[prec], device="cuda")
+        ds = torch.zeros(n, dtype=rdt[prec], device="cuda")
+
+        def svd():
+            dc.copy_(src)
+            stn.dense_svd(prec, m, n, dc.data_ptr(), dv.data_ptr(), ds.data_ptr(), mode)
+        ms = timeit(svd)
+        print(json.dumps({"what": "svd", "precision": "c128" if prec == 0 else "c64", "mode": mode, "m": m, "n": n,
+                          "ms": round(ms, 3), "alg_gflops": round(_svd(m, n) / ms / 1e6, 2)}), flush=True)
+    for prec, m, n in DENSE_QR_CASES:
+        src = torch.tensor(graded(m, n), dtype=cdt[prec], device="cuda")
+        d = src.clone()
+
+        def qr():
+            d.copy_(src)
+            stn.dense_qr(prec, m, n, d.data_ptr())
+        ms = timeit(qr)
+        print(json.dumps({"what": "qr", "precision": "c128" if prec == 0 else "c64", "m": m, "n": n,
+                          "ms": round(ms, 3), "alg_gflops": round(_qr(m, n) / ms / 1e6, 2)}), flush=True)
 
 
 # -- GPU arm -------------------------------------------------------------------
@@ -241,12 +335,18 @@ def main():
     w = D5_BENCH
     if args.chi_cap is not None and args.chi_cap != w.chi_cap:
         w = w.with_(chi_cap=args.chi_cap, name=f"{w.name}_cap{args.chi_cap}")
+    if args.precision == "c128":
+        w = w.with_(precision=PRECISION_C128, svd_cutoff=1e-12, degeneracy_tol=1e-12,
+                    name=w.name.replace("_c64", "_c128"))
     if args.impl == "reference":
         reference_arm(args, w)
         return
+    if args.dense_routines:
+        dense_routines()
+        return
     import torch
     import paper_2605_29514_gb300 as stn
-    from paper_2605_29514_gb300.shards import rank_base
+    from paper_2605_29514_gb300.shards import batch_offset
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -257,21 +357,23 @@ def main():
         pg = dist
     stn.build()
     segs = w.rounds + 1
-    K = max(segs, ((args.steps + segs - 1) // segs) * segs)
+    K = max(1, args.steps)
     W = max(3, args.warmup)
-    B = args.shots
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    B = args.shots if args.shots > 0 else sms
     stream = torch.cuda.current_stream()
+    peaks = measure_peaks(stn, torch, stream)
     sim = stn.Simulator(w, max_shots=B, stream=stream.cuda_stream)
     theta = theta_table(w, sim.n_pairs)
     th_host = torch.tensor(theta, dtype=torch.float64).pin_memory()
     d_theta = torch.empty_like(th_host, device="cuda")
     d_theta.copy_(th_host)
     rec_host = torch.empty((B, sim.rec_bytes), dtype=torch.uint8).pin_memory()
-    base = rank_base(rank)  # disjoint global shot ranges per rank
+    plan, complete = timed_plan(K, segs)
 
     # warm-up: W steps, each the first segment (syndrome round 0) of a fresh batch
     for i in range(W):
-        sim.begin_batch(B, base + i * B)
+        sim.begin_batch(B, batch_offset(rank, i, B))
         sim.apply_round_device(0, d_theta.data_ptr())
     sim.sync()
     torch.cuda.synchronize()
@@ -280,82 +382,94 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    seg_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(segs + 1)] for _ in range(K // segs)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     flops0 = sim.algorithmic_flops()
     prof0 = sim.profile_counters()
     launches = 0
-    # timed: K segments = K / 6 complete batches.  The host clock also covers the
-    # angle upload from pinned memory and each batch's record download (e2e).
+    flops_complete = 0.0
     t_host = time.perf_counter()
     d_theta.copy_(th_host, non_blocking=True)
     ev0.record(stream)
-    for b in range(K // segs):
-        sim.begin_batch(B, base + (W + b) * B)
-        launches += 1
-        for seg in range(segs):
-            seg_ev[b][seg].record(stream)
-            sim.apply_round_device(seg, d_theta.data_ptr())
+    for i, (b, g) in enumerate(plan):
+        if g == 0:
+            sim.begin_batch(B, batch_offset(rank, W + b, B))
             launches += 1
-        seg_ev[b][segs].record(stream)
-        if b + 1 == K // segs:
-            ev1.record(stream)
-        sim.read_records_into(rec_host.data_ptr())
-    host_s = time.perf_counter() - t_host
+        kev[i][0].record(stream)
+        sim.apply_round_device(g, d_theta.data_ptr())
+        kev[i][1].record(stream)
+        launches += 1
+        if g == segs - 1:
+            sim.read_records_into(rec_host.data_ptr())  # synchronises: the batch's records reach the host
+            if b + 1 == complete:
+                flops_complete = sim.algorithmic_flops() - flops0
+    ev1.record(stream)
     torch.cuda.synchronize()
+    host_s = time.perf_counter() - t_host
     flops = sim.algorithmic_flops() - flops0
     prof1 = sim.profile_counters()
     clk = clocks.stop()
-    seg_ms = [statistics.mean(seg_ev[b][g].elapsed_time(seg_ev[b][g + 1]) for b in range(K // segs))
-              for g in range(segs)]
+    secs = ev0.elapsed_time(ev1) / 1000.0
+    kernel_s = sum(a.elapsed_time(z) for a, z in kev) / 1000.0
+    seg_ms = {}
+    for i, (b, g) in enumerate(plan):
+        seg_ms.setdefault(g, []).append(kev[i][0].elapsed_time(kev[i][1]))
     dprof = {k: prof1[k] - prof0[k] for k in prof1}
     loop = max(dprof["op_loop_cycles"], 1.0)
-    phases = {"segment_ms": [round(x, 3) for x in seg_ms],
+    shot_segs = max(1, B * K)
+    phases = {"segment_ms": {str(g): round(statistics.mean(v), 1) for g, v in sorted(seg_ms.items())},
               "cycle_share": {k.replace("_cycles", ""): round(dprof[k] / loop, 4)
-                              for k in ("left_sweep_cycles", "svd_cycles", "right_sweep_rest_cycles",
-                                        "expectation_cycles", "gauge_cycles")},
-              "svds_per_shot": {"shared_memory": dprof["svd_count_shared"] / (B * (K // segs)),
-                                "large_bond": dprof["svd_count_large"] / (B * (K // segs)),
-                                "gauge_sites": dprof["gauge_sites"] / (B * (K // segs))},
-              "source": "stn_profile_counters: SM clock cycles of each CTA per phase, over the timed batches"}
-    secs = ev0.elapsed_time(ev1) / 1000.0
+                              for k in ("left_sweep_cycles", "svd_cycles", "svd_small_cycles",
+                                        "right_sweep_rest_cycles", "expectation_cycles", "gauge_cycles")},
+              "per_shot_segment": {"svds_shared_memory": dprof["svd_count_shared"] / shot_segs,
+                                   "svds_large_bond": dprof["svd_count_large"] / shot_segs,
+                                   "gauge_sites": dprof["gauge_sites"] / shot_segs},
+              "source": "stn_profile_counters: SM clock cycles of each CTA per phase over the timed steps"}
     if pg:
-        t = torch.tensor([secs, host_s], dtype=torch.float64, device="cuda")
+        t = torch.tensor([secs, host_s, kernel_s], dtype=torch.float64, device="cuda")
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        secs, host_s = float(t[0].item()), float(t[1].item())
-    shots_done = ws * B * K // segs
+        secs, host_s, kernel_s = (float(x) for x in t.tolist())
+    if complete > 0:
+        shots_done = ws * B * complete
+        counted = f"{complete} complete batch(es) of {B} shots per rank"
+    else:  # fewer steps than a batch: the fraction of its segments, an estimate
+        shots_done = ws * B * K / segs
+        counted = f"no batch completes in {K} steps: B K / {segs} shot-equivalents (estimate)"
     value = shots_done / secs
     e2e = {"value": shots_done / host_s, "unit": "shots/s",
            "h2d_bytes_per_step": int(th_host.numel() * 8) / K,
-           "d2h_bytes_per_step": int(rec_host.numel()) * (K // segs) / K,
-           "path": "C ABI with host buffers: angles copied from pinned host memory, records read back "
-                   "into pinned host memory after each batch (stn_read_records)"}
+           "d2h_bytes_per_step": int(rec_host.numel()) * complete / K,
+           "path": "C ABI with host buffers: angles copied from pinned host memory, each completed batch's "
+                   "records read back into pinned host memory (stn_read_records)"}
 
-    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
-    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
-    achieved = flops / secs / 1e12 / ws
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
-                "traffic_note": "DRAM bytes of the round kernel are not captured at this workload's size; "
-                                "in a capture at chi cap 16 they were negligible (the path is latency-bound)",
-                "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {max_mhz:.0f} MHz "
-                               "(max SM clock of MEASURED_PEAKS.json)",
-                "kernel": "stn::round_kernel<float>",
-                "work": "algorithmic FLOPs of the MPS sweeps (standard GEMM, Householder QR and SVD counts)"}
+    peak = peaks["fp32_fma"]
+    achieved = flops / kernel_s / 1e12 / ws
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "traffic_note": "DRAM bytes of the round kernel are not captured at this workload's size; the "
+                                "path is bound by on-chip arithmetic and latency, not HBM",
+                "peak_source": "measured in this run: FP32 FMA probe (stn_peak_probe kind 0) on every SM",
+                "peaks_measured_tflops": {k: round(v, 2) for k, v in peaks.items()},
+                "kernel": f"stn::round_kernel<{'float' if w.precision else 'double'}>",
+                "work": "device-counted algorithmic FLOPs of the MPS sweeps (GEMM, Householder R factor and SVD "
+                        "textbook counts) over the summed CUDA-event durations of the timed round-kernel launches"}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        cpu = cpu_baseline(w, args.cpu_seconds, flops / shots_done if flops > 0 else None)
+    if rank == 0 and not args.no_cpu_baseline and ws == 1 and flops > 0 and shots_done > 0:
+        per_shot = flops_complete / (B * complete) if complete > 0 else flops / (B * K / segs)
+        cpu = cpu_baseline(w, args.cpu_seconds, per_shot)
 
     if rank == 0:
-        line = {"metric": "shots/s of d=5, 5-round crosstalk syndrome extraction on 1 GB300 at <=1e-5 Born error",
-                "value": value, "unit": "shots/s", "n_gpus": ws, "steps": K, "warmup": W,
+        line = {"metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": ws, "steps": K, "warmup": W,
                 "ms_per_step": 1000.0 * secs / K, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+                "vs_baseline": None, "dtype": "c64" if w.precision else "c128", "data": "synthetic",
                 "config": {"workload": w.name, "distance": w.distance, "rounds": w.rounds, "theta": w.theta,
                            "p": w.p, "chi_cap": w.chi_cap, "shots_per_batch_per_rank": B,
                            "step": "one program segment (syndrome round or final readout) over the batch",
-                           "l2": "per-shot MPS state (GBs) larger than L2; no flush",
+                           "counted": counted,
+                           "batch_vs_config": f"the configuration's 16,384 shots run as batches of {B} "
+                                              "resident shots (one per SM); a batch's segments are "
+                                              "one launch each",
+                           "l2": "per-shot MPS state (GBs in all) larger than L2; no flush",
                            "parallelism": f"shots sharded over {ws} rank(s)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "phases": phases}

@@ -53,15 +53,25 @@ typedef enum {
 
 enum { STN_PAIRS_ADJACENT_IDLE = 0, STN_PAIRS_ADJACENT_IDLE_DIAG_XX = 1 };
 enum { STN_PRECISION_C128 = 0, STN_PRECISION_C64 = 1 };
+enum { STN_BASIS_Z = 0, STN_BASIS_X = 1 };
 
-/* Simulation parameters.  Rates follow Table I: p1 = p1_scale*p after each
- * single-qubit gate (Eq. 2), p2 = p2_scale*p after each CNOT (Eq. 3),
- * pR = pR_scale*p X flip after each reset, pM = pM_scale*p flip of each
- * recorded bit. */
+/* Simulation parameters: the problem statement of Sec. II-III (code
+ * distance, rounds, CNOT schedule, crosstalk pairs and angles, Pauli noise
+ * rates) and the truncation of Sec. IV B.  Rates follow Table I:
+ * p1 = p1_scale*p after each single-qubit gate (Eq. 2), p2 = p2_scale*p
+ * after each CNOT (Eq. 3), pR = pR_scale*p X flip after each reset,
+ * pM = pM_scale*p flip of each recorded bit.
+ *
+ * Qubits are numbered 0..n-1 in row-major (y, x) order of the layout
+ * (stn_layout gives coordinates and kinds): data qubit (column i, row j) at
+ * (2i+1, 2j+1), face (i, j) at (2i, 2j), X type when i + j is odd.  The
+ * ancillas, in ascending qubit order, index the rows of cnot_schedule.
+ * stn_create deep-copies every array; the caller keeps ownership. */
 typedef struct {
   int32_t distance;      /* code distance d >= 3, odd; n = 2 d^2 - 1 qubits */
-  int32_t rounds;        /* syndrome rounds >= 1 */
-  int32_t pair_rule;     /* STN_PAIRS_*: which pairs get crosstalk (Sec. III B) */
+  int32_t rounds;        /* syndrome rounds >= 1 (Sec. II: d rounds) */
+  int32_t pair_rule;     /* STN_PAIRS_*: which pairs get crosstalk (Sec. III B)
+                            when n_pairs = 0 */
   int32_t chi_cap;       /* bond-dimension cap chi_max (Sec. IV B), 1..256 */
   double p, p1_scale, p2_scale, pR_scale, pM_scale;
   double svd_cutoff;     /* drop Schmidt values <= svd_cutoff * s_1 */
@@ -69,6 +79,29 @@ typedef struct {
                             one by more than degeneracy_tol * s_1 */
   int32_t precision;     /* STN_PRECISION_*: arithmetic of the MPS path */
   uint64_t seed;         /* Philox key */
+  int32_t memory_basis;  /* STN_BASIS_Z: data prepared and read out in Z,
+                            detectors on Z faces, logical Z_L on the top data
+                            row; STN_BASIS_X: H after the data reset and
+                            before the readout, X faces, X_L on the left
+                            data column */
+  int32_t n_pairs;       /* K > 0: the explicit pairs below replace pair_rule */
+  const int32_t *cnot_schedule;  /* [d^2 - 1][4] (ancillas in ascending qubit
+                            order): the data qubit each ancilla's CNOT gates in
+                            layers 0..3 of Fig. 1, or -1 for an idle layer;
+                            every face qubit exactly once, no qubit twice in a
+                            layer.  NULL: the hook-avoiding default (Z faces
+                            NW, SW, NE, SE; X faces NW, NE, SW, SE) */
+  const int32_t *pairs;           /* [K][2] qubits of crosstalk pair k (Eq. 4) */
+  const uint8_t *pair_pauli;      /* [K] 0: exp(-i theta Z Z), 1: X X; NULL = ZZ */
+  const uint8_t *pair_layer_mask; /* [K] bit l: the rotation acts after CNOT
+                            layer l; NULL = after every layer in which no CNOT
+                            acts on exactly that pair (Sec. III B, Fig. 1) */
+  int64_t arena_cap_bytes; /* 0: each resident shot's stack of doubled span
+                            tensors and R factors is sized for the largest
+                            span the cap allows; > 0: that stack is capped at
+                            this many bytes, and a sweep that needs more stops
+                            its shot with STN_EOVERFLOW (reported by the next
+                            synchronising call) */
 } stn_config;
 
 /* Per-shot diagnostics of the last batch (Sec. IV B: truncation). */
@@ -79,10 +112,19 @@ typedef struct {
   double logp;       /* log-probability of the realised outcomes */
 } stn_shot_stats;
 
-/* Compile the program (layout, CNOT schedule, crosstalk pairs, event ids) and
- * allocate device state for up to max_shots shots per batch.  `cuda_stream`
- * is a cudaStream_t (NULL = legacy default stream).  On success *out owns
- * the context.  Errors: STN_EINVAL (bad config), STN_ENOMEM, STN_ECUDA. */
+/* Host-only layout of the distance-d rotated code (Sec. II, Fig. 1; no GPU
+ * needed): h_xy[2n] the (x, y) coordinates of qubit q at h_xy[2q], h_kind[n]
+ * 'D' (data), 'X' or 'Z' (ancilla of that face type); either may be NULL.
+ * Returns n, or -1 for a distance that is not odd and in 3..11. */
+int32_t stn_layout(int32_t distance, int32_t *h_xy, char *h_kind);
+
+/* Compile the program (Sec. II-III: layout, CNOT schedule, crosstalk pairs,
+ * noise events, measurement records) and allocate device state for up to
+ * max_shots shots per batch.  `cuda_stream` is a cudaStream_t (NULL = legacy
+ * default stream).  On success *out owns the context.  Errors: STN_EINVAL
+ * (bad config: distance, rounds, rates, a schedule that does not gate every
+ * face qubit once or gates a qubit twice in a layer, a pair out of range),
+ * STN_ENOMEM, STN_ECUDA. */
 stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_stream,
                       stn_ctx **out);
 void stn_destroy(stn_ctx *ctx);
@@ -167,14 +209,17 @@ stn_status stn_compile_detectors(const stn_config *cfg, int32_t *h_counts, int32
 stn_status stn_algorithmic_flops(stn_ctx *ctx, double *h_total);
 
 /* Phase counters of all round launches since creation, summed over shot
- * slots (synchronises).  h_out[10]: SM clock cycles spent by the CTAs in
+ * slots (synchronises).  h_out[12]: SM clock cycles spent by the CTAs in
  * [0] the left (R-factor) sweep, [1] the right sweep's SVDs, [2] the rest of
  * the right sweep (contractions, sorting, new sites), [3] expectation values,
  * [4] the whole op loop (so [4] - [0..3] - [7] is the tableau and
  * bookkeeping); counts of [5] shared-memory SVDs and [6] large-bond SVDs
  * (Householder R factor plus Jacobi on R^dag); [7] cycles of the gauge steps
  * that move the orthogonality centre into an operator's support and [8] the
- * number of sites they crossed; [9] is zero.  Diagnostics only: they explain
+ * number of sites they crossed; [9] the cycles of the shared-memory SVDs
+ * (a part of [1]); [10] the Jacobi sweeps of the large-bond SVDs and [11]
+ * the cycles of their Householder R factors (a part of [1]).  Diagnostics
+ * only: they explain
  * where a round's time goes, they are not part of the path. */
 stn_status stn_profile_counters(stn_ctx *ctx, double *h_out);
 
@@ -251,7 +296,8 @@ stn_status stn_dense_svd(int32_t precision, int32_t m, int32_t n, void *d_c, voi
  * held from library load until process exit.
  *   d_c: input, ROW-major m x n complex of the precision (device), left
  *        unchanged.  d_v (n x n, column-major), d_sig2[n]: outputs as for
- *        stn_dense_svd with in_shared = 3.  m <= 1024.
+ *        stn_dense_svd with in_shared = 3.  m <= 1024, n <= 512 (the sizes
+ *        of the truncation sweep's bond matrices).
  *   Limit: m n complex elements must fit 1 MiB (m n <= 131072 for
  *   complex64, 65536 for complex128); larger requests return STN_EOVERFLOW
  *   and launch nothing.  Errors: STN_EINVAL for bad sizes or null pointers,
@@ -263,6 +309,17 @@ stn_status stn_dense_svd(int32_t precision, int32_t m, int32_t n, void *d_c, voi
  * them (one stream, or events between streams). */
 stn_status stn_dense_svd_noalloc(int32_t precision, int32_t m, int32_t n, const void *d_c, void *d_v,
                                  void *d_sig2, void *cuda_stream);
+
+/* Arithmetic-peak probe (the paper has no counterpart: it measures the
+ * denominators of the roofline the kernels are placed on).  Launches on
+ * `cuda_stream`, on every SM at full occupancy, a kernel of independent
+ * kind 0: FP32 FMA chains, kind 1: FP64 FMA chains, kind 2: TF32 tensor-core
+ * products (mma.sync m16n8k8, FP32 accumulation), `iters` loop trips each,
+ * and stores in *h_flops the floating-point operations it performs (an FMA
+ * counts 2).  Asynchronous: the caller times the launch (CUDA events on the
+ * same stream) and divides.  Allocates nothing.  Errors: STN_EINVAL for a bad
+ * kind, iters < 1 or a null h_flops; STN_ECUDA for a launch failure. */
+stn_status stn_peak_probe(int32_t kind, int64_t iters, double *h_flops, void *cuda_stream);
 
 #ifdef __cplusplus
 }

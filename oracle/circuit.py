@@ -53,7 +53,10 @@ class Layout:
         return len(self.coords)
 
 
-def build_layout(d):
+def build_layout(d, schedule=None):
+    """Qubits of the distance-d rotated code.  `schedule` (optional) replaces
+    the CNOT order: one 4-tuple per ancilla, in ascending qubit order, of the
+    data qubit each layer gates (or -1 / None for an idle layer)."""
     pts = []
     for j in range(d):
         for i in range(d):
@@ -77,7 +80,33 @@ def build_layout(d):
         x, y = coords[a]
         order = X_ORDER if kind[a] == "X" else Z_ORDER
         slots[a] = [index.get((x + dx, y + dy)) for dx, dy in order]
+    if schedule is not None:
+        slots = schedule_slots(coords, index, ancillas, slots, schedule)
     return Layout(d, coords, data, ancillas, kind, slots, index)
+
+
+def schedule_slots(coords, index, ancillas, default, schedule):
+    """Validate a caller's CNOT schedule: every ancilla gates each of its
+    face's data qubits in exactly one of the four layers, and no qubit takes
+    part in two CNOTs of one layer (Fig. 1: four CNOT layers per round)."""
+    if len(schedule) != len(ancillas):
+        raise ValueError("one schedule row per ancilla")
+    slots = {}
+    busy = [set() for _ in range(4)]
+    for a, row in zip(ancillas, schedule):
+        if len(row) != 4:
+            raise ValueError("four layers per ancilla")
+        got = [None if (q is None or q < 0) else int(q) for q in row]
+        face = sorted(q for q in default[a] if q is not None)
+        if sorted(q for q in got if q is not None) != face:
+            raise ValueError(f"ancilla {a} must gate each of its data qubits once")
+        for l, q in enumerate(got):
+            if q is not None:
+                if q in busy[l] or a in busy[l]:
+                    raise ValueError(f"qubit {q} or {a} gated twice in layer {l}")
+                busy[l].update((q, a))
+        slots[a] = got
+    return slots
 
 
 @dataclass
@@ -110,7 +139,30 @@ def diagonal_xx_pairs(layout):
     return pairs
 
 
-def build_pairs(layout, rule):
+def idle_mask(layout, a, b):
+    """Layers after which a pair (a, b) is idle: all layers except those in
+    which a CNOT acts on exactly this pair (Sec. III B: crosstalk on coupled
+    qubits that are not gated together)."""
+    mask = 0b1111
+    for anc in layout.ancillas:
+        for l, dq in enumerate(layout.slots[anc]):
+            if dq is not None and {anc, dq} == {a, b}:
+                mask &= ~(1 << l)
+    return mask
+
+
+def build_pairs(layout, rule, explicit=None):
+    """Crosstalk pairs: the rule's, or `explicit` = (a, b, pauli, mask) tuples
+    with pauli 'ZZ' or 'XX' and mask the layers after which the pair rotates
+    (None: the layers in which the pair is idle)."""
+    if explicit is not None:
+        pairs = []
+        for a, b, pauli, mask in explicit:
+            a, b = int(a), int(b)
+            if a == b or not (0 <= a < layout.n and 0 <= b < layout.n) or pauli not in ("ZZ", "XX"):
+                raise ValueError(f"bad pair {(a, b, pauli)}")
+            pairs.append(Pair(a, b, pauli, idle_mask(layout, a, b) if mask is None else int(mask) & 0b1111))
+        return pairs
     pairs = adjacent_idle_pairs(layout)
     if rule == "adjacent_idle+diag_xx":
         pairs += diagonal_xx_pairs(layout)
@@ -129,9 +181,10 @@ class Program:
     n_meas: int
     meas_qubit: list  # record index -> qubit
     meas_round: list  # record index -> round (rounds for the final data readout)
+    basis: str = "Z"  # memory basis: data prepared and read out in Z or X
 
 
-def build_program(layout, pairs, rounds):
+def build_program(layout, pairs, rounds, basis="Z"):
     """Op tuples:
     ('RN', q, ev)              reset flip: X on q if u < pR
     ('H', q)                   Hadamard
@@ -146,9 +199,16 @@ def build_program(layout, pairs, rounds):
     rec = 0
     meas_qubit, meas_round = [], []
     n = layout.n
+    if basis not in ("Z", "X"):
+        raise ValueError(basis)
     for q in range(n):
         ops.append(("RN", q, ev))
         ev += 1
+    if basis == "X":  # data qubits start in |+>: H (with its Eq. 2 noise) after the reset
+        for q in layout.data:
+            ops.append(("H", q))
+            ops.append(("D1", q, ev))
+            ev += 1
     xanc = [a for a in layout.ancillas if layout.kind[a] == "X"]
     for r in range(rounds):
         for a in xanc:
@@ -177,35 +237,42 @@ def build_program(layout, pairs, rounds):
             meas_qubit.append(a)
             meas_round.append(r)
             rec += 1
+    if basis == "X":  # X readout of the data: H (with its noise), then Z measurement
+        for q in layout.data:
+            ops.append(("H", q))
+            ops.append(("D1", q, ev))
+            ev += 1
     for q in layout.data:
         ops.append(("M", q, ev, ev + 1, rec, False, -1))
         ev += 2
         meas_qubit.append(q)
         meas_round.append(rounds)
         rec += 1
-    return Program(layout, pairs, rounds, ops, ev, rec, meas_qubit, meas_round)
+    return Program(layout, pairs, rounds, ops, ev, rec, meas_qubit, meas_round, basis)
 
 
 def detectors(program, record):
-    """Detector bits of a Z-memory experiment from one shot's record bits:
-    Z faces in round 0; every face from round 1 on (XOR with the previous
-    round); each Z face once more from the final data readout."""
+    """Detector bits of a memory experiment in basis B (Z or X) from one
+    shot's record bits: the B faces in round 0 (their stabilizers start in a
+    definite state); every face from round 1 on (XOR with the previous
+    round); each B face once more from the final data readout."""
     layout = program.layout
     anc = layout.ancillas
     na = len(anc)
+    basis = program.basis
     out = []
     for r in range(program.rounds):
         for i, a in enumerate(anc):
             m = record[r * na + i]
             if r == 0:
-                if layout.kind[a] == "Z":
+                if layout.kind[a] == basis:
                     out.append(m)
             else:
                 out.append(m ^ record[(r - 1) * na + i])
     base = program.rounds * na
     data_pos = {q: base + i for i, q in enumerate(layout.data)}
     for i, a in enumerate(anc):
-        if layout.kind[a] != "Z":
+        if layout.kind[a] != basis:
             continue
         par = record[(program.rounds - 1) * na + i]
         for dq in layout.slots[a]:
@@ -216,12 +283,15 @@ def detectors(program, record):
 
 
 def logical_z(program, record):
-    """Parity of the final Z readout along the top data row (Z_L)."""
+    """Parity of the final readout along the logical operator of the memory
+    basis: Z_L on the top data row (y = 1), which commutes with the X faces
+    (the X boundary faces lie on the top and bottom rows); X_L on the left
+    data column (x = 1) for an X-memory run, commuting with the Z faces."""
     layout = program.layout
     base = program.rounds * len(layout.ancillas)
     par = 0
     for i, q in enumerate(layout.data):
         x, y = layout.coords[q]
-        if y == 1:
+        if (y == 1 and program.basis == "Z") or (x == 1 and program.basis == "X"):
             par ^= record[base + i]
     return par

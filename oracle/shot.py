@@ -240,9 +240,9 @@ class ShotSim:
 
 
 def make_program(w):
-    layout = build_layout(w.distance)
-    pairs = build_pairs(layout, w.pair_rule)
-    return build_program(layout, pairs, w.rounds)
+    layout = build_layout(w.distance, w.cnot_schedule)
+    pairs = build_pairs(layout, w.pair_rule, w.pairs)
+    return build_program(layout, pairs, w.rounds, w.memory_basis)
 
 
 def run_shot(w, shot, theta=None, program=None, trace=False, max_ops=None):

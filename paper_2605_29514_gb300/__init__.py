@@ -29,19 +29,59 @@ def _ptr(a):
 
 
 def config_from_workload(w):
-    return Config(
+    """stn_config of a workload.  The arrays of an explicit CNOT schedule or
+    explicit pairs stay referenced by the returned object (stn_create copies
+    them)."""
+    cfg = Config(
         distance=w.distance, rounds=w.rounds, pair_rule=PAIR_RULES[w.pair_rule], chi_cap=w.chi_cap,
         p=w.p, p1_scale=w.p1_scale, p2_scale=w.p2_scale, pR_scale=w.pR_scale, pM_scale=w.pM_scale,
         svd_cutoff=w.svd_cutoff, degeneracy_tol=w.degeneracy_tol, precision=w.precision,
-        seed=w.seed)
+        seed=w.seed, memory_basis={"Z": 0, "X": 1}[getattr(w, "memory_basis", "Z")])
+    keep = []
+    schedule = getattr(w, "cnot_schedule", None)
+    if schedule is not None:
+        sch = np.ascontiguousarray([[(-1 if q is None else q) for q in row] for row in schedule], dtype=np.int32)
+        keep.append(sch)
+        cfg.cnot_schedule = sch.ctypes.data
+    pairs = getattr(w, "pairs", None)
+    if pairs is not None:
+        ab = np.ascontiguousarray([[a, b] for a, b, _, _ in pairs], dtype=np.int32).reshape(-1, 2)
+        pauli = np.ascontiguousarray([{"ZZ": 0, "XX": 1}[pp] for _, _, pp, _ in pairs], dtype=np.uint8)
+        keep += [ab, pauli]
+        cfg.n_pairs = len(pairs)
+        cfg.pairs = ab.ctypes.data
+        cfg.pair_pauli = pauli.ctypes.data
+        if all(m is not None for _, _, _, m in pairs):
+            mask = np.ascontiguousarray([m for _, _, _, m in pairs], dtype=np.uint8)
+            keep.append(mask)
+            cfg.pair_layer_mask = mask.ctypes.data
+        elif any(m is not None for _, _, _, m in pairs):
+            raise ValueError("give a layer mask for every explicit pair or for none")
+    cfg._keep = keep
+    return cfg
+
+
+def layout(distance):
+    """Host-only layout (stn_layout): (xy[n, 2] coordinates, kinds 'D'/'X'/'Z')."""
+    lib = load()
+    n = lib.stn_layout(int(distance), None, None)
+    if n < 0:
+        raise StnError(STN_EINVAL, "bad distance")
+    xy = np.zeros((n, 2), dtype=np.int32)
+    kind = ctypes.create_string_buffer(n)
+    lib.stn_layout(int(distance), _ptr(xy), kind)
+    return xy, [chr(c) for c in kind.raw[:n]]
 
 
 class Simulator:
-    """One stn_ctx: a compiled program plus device state for max_shots shots."""
+    """One stn_ctx: a compiled program plus device state for max_shots shots.
+    arena_cap_bytes > 0 caps each resident shot's stack of span tensors (see
+    stn_config)."""
 
-    def __init__(self, workload, max_shots, stream=0):
+    def __init__(self, workload, max_shots, stream=0, arena_cap_bytes=0):
         self.lib = load()
         self.cfg = config_from_workload(workload)
+        self.cfg.arena_cap_bytes = int(arena_cap_bytes)
         ctx = ctypes.c_void_p()
         st = self.lib.stn_create(ctypes.byref(self.cfg), int(max_shots), ctypes.c_void_p(stream),
                                  ctypes.byref(ctx))
@@ -128,14 +168,14 @@ class Simulator:
 
     PROFILE_KEYS = ("left_sweep_cycles", "svd_cycles", "right_sweep_rest_cycles", "expectation_cycles",
                     "op_loop_cycles", "svd_count_shared", "svd_count_large", "gauge_cycles",
-                    "gauge_sites")
+                    "gauge_sites", "svd_small_cycles", "jacobi_sweeps_large", "svd_qr_cycles")
 
     def profile_counters(self):
         """Per-phase SM cycles and SVD counts summed over shot slots since
         creation (see stn_profile_counters)."""
-        buf = (ctypes.c_double * 10)()
+        buf = (ctypes.c_double * 12)()
         self._check(self.lib.stn_profile_counters(self.ctx, ctypes.cast(buf, ctypes.c_void_p)))
-        return dict(zip(self.PROFILE_KEYS, list(buf)[:9]))
+        return dict(zip(self.PROFILE_KEYS, list(buf)))
 
     def read_records_into(self, h_records_ptr):
         """Packed records of the batch into caller-owned host memory
@@ -231,6 +271,17 @@ def philox_uniforms(seed, shot_offset, n_shots, event_offset, n_events, d_out_pt
         raise StnError(st, "stn_philox_uniforms failed")
 
 
+def peak_probe(kind, iters, stream=0):
+    """Launch the arithmetic-peak probe (kind 0 FP32 FMA, 1 FP64 FMA, 2 TF32
+    mma.sync) on `stream`; returns the FLOPs it performs.  The caller times
+    the launch."""
+    flops = ctypes.c_double()
+    st = load().stn_peak_probe(int(kind), int(iters), ctypes.byref(flops), ctypes.c_void_p(stream))
+    if st != STN_OK:
+        raise StnError(st, "stn_peak_probe failed")
+    return flops.value
+
+
 def dense_qr_q(precision, m, n, d_b, d_q, d_work, stream=0):
     st = load().stn_dense_qr_q(int(precision), int(m), int(n), ctypes.c_void_p(d_b), ctypes.c_void_p(d_q),
                                ctypes.c_void_p(d_work), ctypes.c_void_p(stream))
@@ -262,4 +313,4 @@ def dense_svd_noalloc(precision, m, n, d_c, d_v, d_sig2, stream=0):
 
 __all__ = ["Simulator", "StnError", "build", "load", "philox_uniforms", "unpack_records",
            "config_from_workload", "compile_program", "compile_detectors", "dense_qr", "dense_svd",
-           "dense_svd_noalloc"]
+           "dense_svd_noalloc", "peak_probe", "layout"]

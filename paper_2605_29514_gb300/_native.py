@@ -14,7 +14,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libstn.so")
-SOURCES = ["engine_f32.cu", "engine_f64.cu", "engine.cu", "engine_noalloc.cu", "program.cpp", "api.cpp"]
+SOURCES = ["engine_f32.cu", "engine_f64.cu", "engine.cu", "engine_noalloc.cu", "peaks.cu", "program.cpp",
+           "api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
@@ -64,6 +65,13 @@ class Config(ctypes.Structure):
         ("degeneracy_tol", ctypes.c_double),
         ("precision", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
+        ("memory_basis", ctypes.c_int32),
+        ("n_pairs", ctypes.c_int32),
+        ("cnot_schedule", ctypes.c_void_p),
+        ("pairs", ctypes.c_void_p),
+        ("pair_pauli", ctypes.c_void_p),
+        ("pair_layer_mask", ctypes.c_void_p),
+        ("arena_cap_bytes", ctypes.c_int64),
     ]
 
 
@@ -81,6 +89,7 @@ EXPORTS = [
     ("stn_create", ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int64, ctypes.c_void_p,
                                   ctypes.POINTER(ctypes.c_void_p)]),
     ("stn_destroy", None, [ctypes.c_void_p]),
+    ("stn_layout", ctypes.c_int32, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     ("stn_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("stn_num_qubits", ctypes.c_int32, [ctypes.c_void_p]),
     ("stn_num_pairs", ctypes.c_int32, [ctypes.c_void_p]),
@@ -120,6 +129,8 @@ EXPORTS = [
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     ("stn_dense_svd_noalloc", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("stn_peak_probe", ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.c_void_p]),
     ("stn_philox_uniforms", ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                            ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p,
                                            ctypes.c_void_p]),

@@ -132,12 +132,67 @@ std::string validate(const stn_config *cfg) {
   if (!(cfg->degeneracy_tol >= 0.0) || !(cfg->degeneracy_tol < 1.0))
     return "degeneracy_tol must be in [0, 1)";
   if (cfg->distance > 9) return "distance must be <= 9";
+  if (cfg->memory_basis != STN_BASIS_Z && cfg->memory_basis != STN_BASIS_X)
+    return "memory_basis must be STN_BASIS_Z or STN_BASIS_X";
+  if (cfg->n_pairs < 0 || cfg->n_pairs > 4096) return "n_pairs must be 0..4096";
+  if (cfg->n_pairs > 0 && !cfg->pairs) return "pairs is NULL with n_pairs > 0";
+  if (cfg->arena_cap_bytes < 0) return "arena_cap_bytes must be >= 0";
   return std::string();
+}
+
+// The program spec of a validated config, with the caller's arrays copied.
+std::string make_spec(const stn_config *cfg, stn::ProgramSpec &sp) {
+  std::string why = validate(cfg);
+  if (!why.empty()) return why;
+  sp = stn::ProgramSpec();
+  sp.d = cfg->distance;
+  sp.rounds = cfg->rounds;
+  sp.pair_rule = cfg->pair_rule;
+  sp.basis = cfg->memory_basis;
+  if (cfg->cnot_schedule) {
+    const int n_anc = cfg->distance * cfg->distance - 1;
+    sp.schedule.assign(cfg->cnot_schedule, cfg->cnot_schedule + 4 * n_anc);
+  }
+  if (cfg->n_pairs > 0) {
+    sp.explicit_pairs = true;
+    for (int k = 0; k < cfg->n_pairs; ++k) {
+      stn::Pair p{};
+      p.a = cfg->pairs[2 * k];
+      p.b = cfg->pairs[2 * k + 1];
+      p.pauli = cfg->pair_pauli ? cfg->pair_pauli[k] : 0;
+      p.layer_mask = cfg->pair_layer_mask ? (cfg->pair_layer_mask[k] & 0xF) : -1;
+      sp.pairs.push_back(p);
+    }
+  }
+  return std::string();
+}
+
+std::string compile(const stn_config *cfg, stn::Program &prog) {
+  stn::ProgramSpec sp;
+  std::string why = make_spec(cfg, sp);
+  if (!why.empty()) return why;
+  return stn::build_program(sp, prog);
 }
 
 }  // namespace
 
 extern "C" {
+
+int32_t stn_layout(int32_t distance, int32_t *h_xy, char *h_kind) {
+  stn::ProgramSpec sp;
+  sp.d = distance;
+  sp.rounds = 1;
+  stn::Program prog;
+  if (!stn::build_program(sp, prog).empty()) return -1;
+  for (int q = 0; q < prog.n; ++q) {
+    if (h_xy) {
+      h_xy[2 * q] = prog.xy[2 * q];
+      h_xy[2 * q + 1] = prog.xy[2 * q + 1];
+    }
+    if (h_kind) h_kind[q] = prog.kind[q];
+  }
+  return prog.n;
+}
 
 stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_stream, stn_ctx **out) {
   if (!out) return STN_EINVAL;
@@ -148,9 +203,14 @@ stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_strea
   stn_ctx *c = new (std::nothrow) stn_ctx();
   if (!c) return STN_ENOMEM;
   c->cfg = *cfg;
+  // the arrays were copied into the program; the context keeps no caller pointer
+  c->cfg.cnot_schedule = nullptr;
+  c->cfg.pairs = nullptr;
+  c->cfg.pair_pauli = nullptr;
+  c->cfg.pair_layer_mask = nullptr;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   c->max_shots = max_shots;
-  why = stn::build_program(cfg->distance, cfg->rounds, cfg->pair_rule, c->prog);
+  why = compile(cfg, c->prog);
   if (!why.empty()) {
     delete c;
     return STN_EINVAL;
@@ -172,6 +232,16 @@ stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_strea
     c->site_off[k + 1] = c->site_off[k] + 2ll * c->chimax[k] * c->chimax[k + 1];
   c->slab_elems = c->site_off[n];
   c->plan = stn::plan_scratch(n, c->chimax.data(), cfg->chi_cap);
+  if (cfg->arena_cap_bytes > 0) {  // shrink the span stacks to the caller's cap
+    const int64_t cap = cfg->arena_cap_bytes / static_cast<int64_t>(c->elem);
+    const int64_t need = c->plan.ap_elems + c->plan.g_elems;
+    if (cap < need) {
+      const double f = static_cast<double>(cap) / static_cast<double>(need);
+      c->plan.ap_elems = static_cast<int64_t>(static_cast<double>(c->plan.ap_elems) * f);
+      c->plan.g_elems = static_cast<int64_t>(static_cast<double>(c->plan.g_elems) * f);
+      c->plan.total = c->plan.ap_elems + c->plan.g_elems + c->plan.work_elems;
+    }
+  }
   c->svd_elems = stn::round_kernel_svd_elems(cfg->precision, n, c->W);
   if (c->svd_elems < 2 * 4 * c->plan.work_c + 16) {  // the blocked SVD needs two columns
     delete c;
@@ -287,9 +357,8 @@ stn_status stn_get_program(const stn_ctx *c, int32_t *h_ops, int32_t *h_pairs) {
 
 stn_status stn_compile_program(const stn_config *cfg, int32_t *h_counts, int32_t *h_ops,
                                int32_t *h_pairs) {
-  if (!validate(cfg).empty()) return STN_EINVAL;
   stn::Program prog;
-  if (!stn::build_program(cfg->distance, cfg->rounds, cfg->pair_rule, prog).empty()) return STN_EINVAL;
+  if (!compile(cfg, prog).empty()) return STN_EINVAL;
   if (h_counts) {
     h_counts[0] = prog.n;
     h_counts[1] = static_cast<int32_t>(prog.pairs.size());
@@ -303,9 +372,8 @@ stn_status stn_compile_program(const stn_config *cfg, int32_t *h_counts, int32_t
 
 stn_status stn_compile_detectors(const stn_config *cfg, int32_t *h_counts, int32_t *h_det,
                                  int32_t *h_logical) {
-  if (!validate(cfg).empty()) return STN_EINVAL;
   stn::Program prog;
-  if (!stn::build_program(cfg->distance, cfg->rounds, cfg->pair_rule, prog).empty()) return STN_EINVAL;
+  if (!compile(cfg, prog).empty()) return STN_EINVAL;
   if (h_counts) {
     h_counts[0] = prog.n_det;
     h_counts[1] = static_cast<int32_t>(prog.logical.size());
@@ -526,7 +594,7 @@ stn_status stn_dense_svd(int32_t precision, int32_t m, int32_t n, void *d_c, voi
 
 stn_status stn_dense_svd_noalloc(int32_t precision, int32_t m, int32_t n, const void *d_c, void *d_v,
                                  void *d_sig2, void *cuda_stream) {
-  if ((precision != 0 && precision != 1) || m < 1 || n < 1 || m > 1024 || !d_c || !d_v || !d_sig2)
+  if ((precision != 0 && precision != 1) || m < 1 || n < 1 || m > 1024 || n > 512 || !d_c || !d_v || !d_sig2)
     return STN_EINVAL;
   if (2 * m + 4 > stn::svd_smem_elems(precision) || 2 * n + 4 > stn::svd_smem_elems(precision))
     return STN_EINVAL;

@@ -8,15 +8,17 @@
 
 namespace stn {
 
-constexpr int kThreads = 256;   // threads per CTA of the round kernel
+constexpr int kThreads = 512;   // threads per CTA of the round kernel (16 warps)
 constexpr double kNearThreshold = 1e-5;
 // Phase counters (SM clock cycles of the CTA, summed over ops): left sweep,
 // right-sweep SVDs, the rest of the right sweep, expectation values, the whole
 // op loop; counts of small (shared-memory) and large-bond SVDs; gauge-move
-// cycles and the number of sites they crossed.
-constexpr int kProfSlots = 10;
+// cycles and the number of sites they crossed; the cycles of the small SVDs
+// (a part of the SVD cycles); the Jacobi sweeps of the large-bond SVDs and
+// the cycles of their Householder R factors (a part of the SVD cycles).
+constexpr int kProfSlots = 12;
 enum ProfSlot { PROF_LEFT = 0, PROF_SVD, PROF_RIGHT, PROF_EXPECT, PROF_OPS, PROF_NSVD_SMALL,
-                PROF_NSVD_LARGE, PROF_GAUGE, PROF_NGAUGE, PROF_SPARE };
+                PROF_NSVD_LARGE, PROF_GAUGE, PROF_NGAUGE, PROF_SVD_SMALL, PROF_JSWEEPS, PROF_SVD_QR };
 
 // Everything one segment launch needs.  Per-shot arrays are indexed by the
 // shot's position in the batch; per-CTA scratch by blockIdx.x.

@@ -142,15 +142,17 @@ static __device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t 
 // CTA-wide helpers
 static __device__ __forceinline__ int tid() { return threadIdx.x; }
 
-// Sum of one double per thread over the CTA (red: kThreads doubles of smem).
+// Sum of one double per thread over the CTA: a shuffle reduction per warp,
+// then every thread adds the warps' partial sums (red: kThreads doubles of
+// smem, of which the first kThreads / 32 are used).  Two barriers.
 static __device__ double block_sum(double v, double *red) {
-  red[tid()] = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  for (int s = kThreads / 2; s > 0; s >>= 1) {
-    if (tid() < s) red[tid()] += red[tid() + s];
-    __syncthreads();
-  }
-  double r = red[0];
+  double r = 0.0;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) r += red[w];
   __syncthreads();
   return r;
 }
@@ -161,15 +163,19 @@ template <typename T, int TA, int TB>
 static __device__ void cgemm(int M, int N, int K, cplx<T> alpha, const cplx<T> *A, int lda,
                       const cplx<T> *B, int ldb, cplx<T> beta, cplx<T> *C, int ldc,
                       cplx<T> *tile) {
+  // thread (ty, tx) of a kTY x 16 grid owns rows ty + kTY a (a < kMR) and
+  // columns tx + 16 b (b < 4) of the 64 x 64 output tile
+  constexpr int kTY = kThreads / 16, kMR = kBM / kTY;
+  static_assert(kMR * kTY == kBM && (kBM * kBK) % kThreads == 0, "tile shape");
   cplx<T> *As = tile;                    // [kBK][kBM + kPad]
   cplx<T> *Bs = tile + kBK * (kBM + kPad);  // [kBK][kBN + kPad]
   const int ty = tid() / 16, tx = tid() % 16;
   const int tilesM = (M + kBM - 1) / kBM, tilesN = (N + kBN - 1) / kBN;
   for (int t = 0; t < tilesM * tilesN; ++t) {
     const int i0 = (t / tilesN) * kBM, j0 = (t % tilesN) * kBN;
-    cplx<T> acc[4][4];
+    cplx<T> acc[kMR][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < kMR; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[a][b] = cmake<T>(0, 0);
     for (int k0 = 0; k0 < K; k0 += kBK) {
@@ -199,21 +205,21 @@ static __device__ void cgemm(int M, int N, int K, cplx<T> alpha, const cplx<T> *
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < kBK; ++k) {
-        cplx<T> av[4], bv[4];
+        cplx<T> av[kMR], bv[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = As[k * (kBM + kPad) + ty + 16 * a];
+        for (int a = 0; a < kMR; ++a) av[a] = As[k * (kBM + kPad) + ty + kTY * a];
 #pragma unroll
         for (int b = 0; b < 4; ++b) bv[b] = Bs[k * (kBN + kPad) + tx + 16 * b];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < kMR; ++a)
 #pragma unroll
           for (int b = 0; b < 4; ++b) cfma(acc[a][b], av[a], bv[b]);
       }
       __syncthreads();
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      int gi = i0 + ty + 16 * a;
+    for (int a = 0; a < kMR; ++a) {
+      int gi = i0 + ty + kTY * a;
       if (gi >= M) continue;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
@@ -250,26 +256,26 @@ __device__ __forceinline__ T warp_sum(T v) {
 // T_kk = 2, T[0:k, k] = -2 T[0:k, 0:k] V[:, 0:k]^dag u_k) is applied to the
 // trailing columns at once, one thread per column, so the trailing matrix is
 // read and written twice per panel rather than per column.  pbuf needs
-// m nb + 2 nb^2 complex elements (nb is reduced to fit).  CTA-wide.
+// m (nb + 1) + 2 nb^2 complex elements (nb is reduced to fit).  CTA-wide.
 constexpr int kQrPanel = 16;
 
 static __device__ __forceinline__ int qr_panel_width(int m, int pbuf_elems) {
   int nb = kQrPanel;
-  while (nb > 1 && static_cast<int64_t>(m) * nb + 2 * nb * nb > pbuf_elems) --nb;
+  while (nb > 1 && static_cast<int64_t>(m) * (nb + 1) + 2 * nb * nb > pbuf_elems) --nb;
   return nb;
 }
 
 // T of the compact WY form of a panel's reflectors (columns of Vp, row-major
-// [mr][nb], u_b zero above row b): T upper triangular, T_kk = 2,
+// [mr][ldv], u_b zero above row b): T upper triangular, T_kk = 2,
 // T[0:k, k] = -2 T[0:k, 0:k] (V[:, 0:k]^dag u_k).  G is scratch.  CTA-wide.
 template <typename T>
-static __device__ void wy_t_factor(int mr, int jb, int nb, const cplx<T> *Vp, cplx<T> *Tm, cplx<T> *G) {
+static __device__ void wy_t_factor(int mr, int jb, int nb, int ldv, const cplx<T> *Vp, cplx<T> *Tm, cplx<T> *G) {
   for (int pr = warp_id(); pr < jb * jb; pr += kWarps) {
     const int a = pr / jb, b = pr % jb;
     if (a >= b) continue;
     T gr = 0, gi = 0;
     for (int i = b + lane_id(); i < mr; i += 32) {  // u_b vanishes above row b
-      const cplx<T> x = Vp[i * nb + a], y = Vp[i * nb + b];
+      const cplx<T> x = Vp[i * ldv + a], y = Vp[i * ldv + b];
       gr += x.re * y.re + x.im * y.im;
       gi += x.re * y.im - x.im * y.re;
     }
@@ -299,33 +305,36 @@ static __device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *p
                              double *dm, cplx<T> *vstore = nullptr) {
   const int steps = min(m, n);
   const int nb = qr_panel_width(m, pbuf_elems);
-  cplx<T> *Vp = pbuf;                                   // [(m - j0)][nb], row-major
-  cplx<T> *Tm = pbuf + static_cast<int64_t>(m) * nb;  // [nb][nb]
+  // rows of the panel padded to an odd number of elements, so that a column
+  // walked by consecutive threads spreads over the shared-memory banks
+  const int ldv = nb + 1;
+  cplx<T> *Vp = pbuf;                                    // [(m - j0)][ldv], row-major
+  cplx<T> *Tm = pbuf + static_cast<int64_t>(m) * ldv;  // [nb][nb]
   cplx<T> *G = Tm + nb * nb;                            // [nb][nb], G[a][b] = u_a^dag u_b
   for (int j0 = 0; j0 < steps; j0 += nb) {
     const int jb = min(nb, steps - j0);
     const int mr = m - j0;
     for (int e = tid(); e < mr * jb; e += kThreads) {
       const int i = e / jb, c = e % jb;
-      Vp[i * nb + c] = B[static_cast<int64_t>(j0 + i) * ld + j0 + c];
+      Vp[i * ldv + c] = B[static_cast<int64_t>(j0 + i) * ld + j0 + c];
     }
     __syncthreads();
     for (int jj = 0; jj < jb; ++jj) {
       double nx2 = 0;
-      for (int i = jj + tid(); i < mr; i += kThreads) nx2 += cabs2d(Vp[i * nb + jj]);
+      for (int i = jj + tid(); i < mr; i += kThreads) nx2 += cabs2d(Vp[i * ldv + jj]);
       nx2 = block_sum(nx2, red);
       // rows above the diagonal of this column are final R entries
-      for (int i = tid(); i < jj; i += kThreads) B[static_cast<int64_t>(j0 + i) * ld + j0 + jj] = Vp[i * nb + jj];
+      for (int i = tid(); i < jj; i += kThreads) B[static_cast<int64_t>(j0 + i) * ld + j0 + jj] = Vp[i * ldv + jj];
       if (!(nx2 > 1e-60)) {  // (numerically) zero column: no reflector, R row jj is final
         for (int i = tid(); i < mr; i += kThreads) {
           if (i >= jj) B[static_cast<int64_t>(j0 + i) * ld + j0 + jj] = cmake<T>(0, 0);
-          Vp[i * nb + jj] = cmake<T>(0, 0);
+          Vp[i * ldv + jj] = cmake<T>(0, 0);
         }
         __syncthreads();
         continue;
       }
       if (tid() == 0) {
-        cplx<T> al = Vp[jj * nb + jj];
+        cplx<T> al = Vp[jj * ldv + jj];
         double aa = sqrt(cabs2d(al));
         double nx = sqrt(nx2);
         double pr = aa > 0 ? al.re / aa : 1.0, pi = aa > 0 ? al.im / aa : 0.0;
@@ -339,19 +348,19 @@ static __device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *p
       for (int i = tid(); i < mr; i += kThreads) {
         cplx<T> u = cmake<T>(0, 0);
         if (i >= jj) {
-          cplx<T> x = Vp[i * nb + jj];
+          cplx<T> x = Vp[i * ldv + jj];
           if (i == jj) x = cmake<T>(x.re - gam.re, x.im - gam.im);
           u = cscale(x, sc);
           B[static_cast<int64_t>(j0 + i) * ld + j0 + jj] = i == jj ? gam : cmake<T>(0, 0);
         }
-        Vp[i * nb + jj] = u;
+        Vp[i * ldv + jj] = u;
       }
       __syncthreads();
       // the rest of the panel: b <- b - 2 u (u^dag b), one warp per column
       for (int c = jj + 1 + warp_id(); c < jb; c += kWarps) {
         T sr = 0, si = 0;
         for (int i = jj + lane_id(); i < mr; i += 32) {
-          const cplx<T> u = Vp[i * nb + jj], b = Vp[i * nb + c];
+          const cplx<T> u = Vp[i * ldv + jj], b = Vp[i * ldv + c];
           sr += u.re * b.re + u.im * b.im;
           si += u.re * b.im - u.im * b.re;
         }
@@ -359,8 +368,8 @@ static __device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *p
         si = __shfl_sync(0xffffffffu, warp_sum(si), 0);
         const cplx<T> s2 = cmake<T>(T(2) * sr, T(2) * si);
         for (int i = jj + lane_id(); i < mr; i += 32) {
-          const cplx<T> t = cmul(Vp[i * nb + jj], s2);
-          cplx<T> &b = Vp[i * nb + c];
+          const cplx<T> t = cmul(Vp[i * ldv + jj], s2);
+          cplx<T> &b = Vp[i * ldv + c];
           b = cmake<T>(b.re - t.re, b.im - t.im);
         }
       }
@@ -369,13 +378,13 @@ static __device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *p
     if (vstore != nullptr)
       for (int e = tid(); e < mr * jb; e += kThreads) {
         const int i = e / jb, c = e % jb;
-        vstore[static_cast<int64_t>(j0 + i) * steps + j0 + c] = Vp[i * nb + c];
+        vstore[static_cast<int64_t>(j0 + i) * steps + j0 + c] = Vp[i * ldv + c];
       }
     if (j0 + jb >= n) {  // no trailing columns
       __syncthreads();
       continue;
     }
-    wy_t_factor<T>(mr, jb, nb, Vp, Tm, G);
+    wy_t_factor<T>(mr, jb, nb, ldv, Vp, Tm, G);
     // trailing columns: b <- b - V (T^dag (V^dag b)); rows go four at a
     // time so that four loads per thread are in flight
     for (int c = j0 + jb + tid(); c < n; c += kThreads) {
@@ -391,13 +400,13 @@ static __device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *p
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int k = 0; k < kQrPanel; ++k)
-            if (k < jb) cfma(w[k], cconj(Vp[(i + u) * nb + k]), b[u]);
+            if (k < jb) cfma(w[k], cconj(Vp[(i + u) * ldv + k]), b[u]);
       }
       for (; i < mr; ++i) {
         const cplx<T> b = B[static_cast<int64_t>(j0 + i) * ld + c];
 #pragma unroll
         for (int k = 0; k < kQrPanel; ++k)
-          if (k < jb) cfma(w[k], cconj(Vp[i * nb + k]), b);
+          if (k < jb) cfma(w[k], cconj(Vp[i * ldv + k]), b);
       }
       // w <- T^dag w in place, highest index first: w'[a] = sum_{b<=a} conj(T[b][a]) w[b]
 #pragma unroll
@@ -417,7 +426,7 @@ static __device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *p
 #pragma unroll
           for (int k = 0; k < kQrPanel; ++k)
             if (k < jb) {
-              const cplx<T> t = cmul(Vp[(i + u) * nb + k], w[k]);
+              const cplx<T> t = cmul(Vp[(i + u) * ldv + k], w[k]);
               b[u] = cmake<T>(b[u].re - t.re, b[u].im - t.im);
             }
           B[static_cast<int64_t>(j0 + i + u) * ld + c] = b[u];
@@ -429,7 +438,7 @@ static __device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *p
 #pragma unroll
         for (int k = 0; k < kQrPanel; ++k)
           if (k < jb) {
-            const cplx<T> t = cmul(Vp[i * nb + k], w[k]);
+            const cplx<T> t = cmul(Vp[i * ldv + k], w[k]);
             acc = cmake<T>(acc.re - t.re, acc.im - t.im);
           }
         bref = acc;
@@ -447,8 +456,9 @@ static __device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *p
 template <typename T>
 static __device__ void form_q(int m, int steps, const cplx<T> *vstore, cplx<T> *Q, cplx<T> *pbuf, int pbuf_elems) {
   const int nb = qr_panel_width(m, pbuf_elems);
+  const int ldv = nb + 1;
   cplx<T> *Vp = pbuf;
-  cplx<T> *Tm = pbuf + static_cast<int64_t>(m) * nb;
+  cplx<T> *Tm = pbuf + static_cast<int64_t>(m) * ldv;
   cplx<T> *G = Tm + nb * nb;
   for (int64_t e = tid(); e < static_cast<int64_t>(m) * steps; e += kThreads) {
     const int i = static_cast<int>(e / steps), c = static_cast<int>(e % steps);
@@ -460,10 +470,10 @@ static __device__ void form_q(int m, int steps, const cplx<T> *vstore, cplx<T> *
     for (int e = tid(); e < mr * nb; e += kThreads) {
       const int i = e / nb, c = e % nb;
       // u_c is zero above its own row; rows above were never written
-      Vp[e] = (c < jb && i >= c) ? vstore[static_cast<int64_t>(j0 + i) * steps + j0 + c] : cmake<T>(0, 0);
+      Vp[i * ldv + c] = (c < jb && i >= c) ? vstore[static_cast<int64_t>(j0 + i) * steps + j0 + c] : cmake<T>(0, 0);
     }
     __syncthreads();
-    wy_t_factor<T>(mr, jb, nb, Vp, Tm, G);
+    wy_t_factor<T>(mr, jb, nb, ldv, Vp, Tm, G);
     for (int c = j0 + tid(); c < steps; c += kThreads) {
       cplx<T> w[kQrPanel];
 #pragma unroll
@@ -477,13 +487,13 @@ static __device__ void form_q(int m, int steps, const cplx<T> *vstore, cplx<T> *
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int k = 0; k < kQrPanel; ++k)
-            if (k < jb) cfma(w[k], cconj(Vp[(i + u) * nb + k]), q[u]);
+            if (k < jb) cfma(w[k], cconj(Vp[(i + u) * ldv + k]), q[u]);
       }
       for (; i < mr; ++i) {
         const cplx<T> q = Q[static_cast<int64_t>(j0 + i) * steps + c];
 #pragma unroll
         for (int k = 0; k < kQrPanel; ++k)
-          if (k < jb) cfma(w[k], cconj(Vp[i * nb + k]), q);
+          if (k < jb) cfma(w[k], cconj(Vp[i * ldv + k]), q);
       }
       // w <- T w in place, lowest index first: w'[a] = sum_{b>=a} T[a][b] w[b]
 #pragma unroll
@@ -501,7 +511,7 @@ static __device__ void form_q(int m, int steps, const cplx<T> *vstore, cplx<T> *
 #pragma unroll
         for (int k = 0; k < kQrPanel; ++k)
           if (k < jb) {
-            const cplx<T> t = cmul(Vp[i * nb + k], w[k]);
+            const cplx<T> t = cmul(Vp[i * ldv + k], w[k]);
             acc = cmake<T>(acc.re - t.re, acc.im - t.im);
           }
         qref = acc;
@@ -611,11 +621,13 @@ constexpr int kMaxBlockedSweepsF = 30, kMaxBlockedSweepsD = 40;
 
 // Unblocked: C and V wherever they are (shared memory for small problems).
 template <typename T>
-static __device__ void svd_onesided(int m, int n, cplx<T> *C, cplx<T> *V, T *sig2, int *flag, double *red) {
+static __device__ int svd_onesided(int m, int n, cplx<T> *C, cplx<T> *V, T *sig2, int *flag, double *red) {
   const T negligible = onesided_prologue<T>(m, n, C, V, red);
   const T tol = onesided_tol<T>(m);
   const int max_sweeps = sizeof(T) == 4 ? kMaxSweepsF : kMaxSweepsD;
+  int sweeps = 0;
   for (int sweep = 0; sweep < max_sweeps && n > 1; ++sweep) {
+    ++sweeps;
     if (tid() == 0) *flag = 0;
     __syncthreads();
     onesided_sweep<T>(m, n, C, V, n, tol, negligible, flag);
@@ -624,6 +636,7 @@ static __device__ void svd_onesided(int m, int n, cplx<T> *C, cplx<T> *V, T *sig
     if (!f) break;
   }
   onesided_epilogue<T>(m, n, C, sig2);
+  return sweeps;
 }
 
 // Blocked, for problems larger than shared memory: C (m x n, column-major)
@@ -702,17 +715,202 @@ static __device__ void jacobi_rotate_staged(int m, int w, cplx<T> *Cb, cplx<T> *
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident cross visit of the blocked Jacobi SVD (complex64, no V).
+// The two column blocks I and J (16 columns each, the last one possibly
+// shorter and zero-padded) of C (m x n, column-major, m <= 256 R) are held in
+// registers, thread t owning rows t, t + 256, ... of all 32 columns.  Step s
+// (s = 0..15) rotates the 16 disjoint cross pairs (I_b, J_{(b+s) mod 16}):
+// every thread forms its rows' contributions to the 16 complex dot products,
+// one CTA-wide reduction sums them, 16 threads turn them into rotations
+// (the same Hestenes rotation as onesided_sweep), and every thread applies
+// them to its rows.  The J registers are then shifted by one slot, so the
+// pairing stays slot b with slot b and all register indices are static.
+// Column norms are reduced once per visit and then updated with the exact
+// one-sided Jacobi identities |x'|^2 = |x|^2 - t|g|, |y'|^2 = |y|^2 + t|g|.
+// Each column is read and written once per visit, instead of twice per pair.
+// wrk: 8 * 32 + 64 + 32 floats of shared memory.  Returns whether any pair
+// rotated (the columns are written back only then).
+
+// Reduce-scatter of 32 values over a warp: lane l returns the warp sum of v[l].
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool upper = (lane & h) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float a = v[i], b = v[i + h];
+      const float send = upper ? a : b;
+      const float keep = upper ? b : a;
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
+  }
+  return v[0];
+}
+
+// CTA sum of 32 values per thread: thread i < 32 returns the sum of value i.
+// Contains one barrier; red holds kWarps * 32 floats.
+__device__ __forceinline__ float cta_reduce32(float (&v)[32], float *red) {
+  const float s = warp_reduce_scatter32(v);
+  red[warp_id() * 32 + lane_id()] = s;
+  __syncthreads();
+  float tot = 0.f;
+  if (tid() < 32) {
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) tot += red[w * 32 + tid()];
+  }
+  return tot;
+}
+
+constexpr int kRvWrkFloats = kWarps * 32 + 64 + 32 + 4;
+// sorted eigenvalues of a bond (at most 512) and, during an SVD, the
+// register-visit reductions
+constexpr int kLamElems = kRvWrkFloats > 512 ? kRvWrkFloats : 512;
+
+template <int R>
+static __device__ bool cross_visit_regs(int m, cplx<float> *C, int c0, int wI, int c1, int wJ, float tol,
+                                        float negligible, float *wrk) {
+  float *red = wrk;                   // kWarps * 32
+  float4 *prm = reinterpret_cast<float4 *>(wrk + kWarps * 32);  // 16 rotations
+  float *nrm = wrk + kWarps * 32 + 64;  // 32 column norms: I then J (in J's column order)
+  int *rot = reinterpret_cast<int *>(nrm + 32);
+  cplx<float> xi[R][16], xj[R][16];
+  const int t = tid();
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int row = t + r * kThreads;
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      xi[r][b] = (row < m && b < wI) ? C[static_cast<int64_t>(c0 + b) * m + row] : cmake<float>(0.f, 0.f);
+      xj[r][b] = (row < m && b < wJ) ? C[static_cast<int64_t>(c1 + b) * m + row] : cmake<float>(0.f, 0.f);
+    }
+  }
+  {
+    float v[32];
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      float a = 0.f, c = 0.f;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        a += cabs2(xi[r][b]);
+        c += cabs2(xj[r][b]);
+      }
+      v[b] = a;
+      v[16 + b] = c;
+    }
+    const float s = cta_reduce32(v, red);
+    if (t < 32) nrm[t] = s;
+    if (t == 0) *rot = 0;
+  }
+  __syncthreads();
+  for (int step = 0; step < 16; ++step) {
+    float v[32];
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      float gr = 0.f, gi = 0.f;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const cplx<float> x = xi[r][b], y = xj[r][b];
+        gr += x.re * y.re + x.im * y.im;  // conj(x) y
+        gi += x.re * y.im - x.im * y.re;
+      }
+      v[2 * b] = gr;
+      v[2 * b + 1] = gi;
+    }
+    const float s = cta_reduce32(v, red);
+    if (t < 32) {
+      const float gi = __shfl_down_sync(0xffffffffu, s, 1);
+      if ((t & 1) == 0) {
+        const int b = t >> 1, jb = (b + step) & 15;
+        const float gr = s, al = nrm[b], be = nrm[16 + jb];
+        float4 p = make_float4(1.f, 0.f, 1.f, 0.f);  // identity: skipped
+        if (al > negligible && be > negligible) {
+          const float absg = sqrtf(gr * gr + gi * gi);
+          if (absg > tol * sqrtf(al) * sqrtf(be)) {
+            const float zeta = (be - al) / (2.f * absg);
+            const float az = fabsf(zeta);
+            float tt = az > 1e10f ? 0.5f / az : 1.f / (az + sqrtf(1.f + zeta * zeta));
+            if (zeta < 0.f) tt = -tt;
+            const float cs = 1.f / sqrtf(1.f + tt * tt), sn = tt * cs;
+            p = make_float4(cs, sn, gr / absg, -gi / absg);  // conj(g / |g|)
+            nrm[b] = fmaxf(al - tt * absg, 0.f);
+            nrm[16 + jb] = fmaxf(be + tt * absg, 0.f);
+            *rot = 1;
+          }
+        }
+        prm[b] = p;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      const float4 p = prm[b];
+      if (p.x != 1.f || p.y != 0.f || p.z != 1.f || p.w != 0.f) {  // uniform over the CTA
+        const cplx<float> uc = cmake<float>(p.z, p.w);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const cplx<float> x = xi[r][b], y = cmul(uc, xj[r][b]);
+          xi[r][b] = cmake<float>(p.x * x.re - p.y * y.re, p.x * x.im - p.y * y.im);
+          xj[r][b] = cmake<float>(p.y * x.re + p.x * y.re, p.y * x.im + p.x * y.im);
+        }
+      }
+    }
+    // slot b of J now pairs with I_b at the next step: shift J by one slot
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const cplx<float> first = xj[r][0];
+#pragma unroll
+      for (int b = 0; b < 15; ++b) xj[r][b] = xj[r][b + 1];
+      xj[r][15] = first;
+    }
+  }
+  __syncthreads();
+  const bool rotated = *rot != 0;
+  if (rotated) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int row = t + r * kThreads;
+      if (row >= m) continue;
+#pragma unroll
+      for (int b = 0; b < 16; ++b) {
+        if (b < wI) C[static_cast<int64_t>(c0 + b) * m + row] = xi[r][b];
+        if (b < wJ) C[static_cast<int64_t>(c1 + b) * m + row] = xj[r][b];
+      }
+    }
+  }
+  __syncthreads();
+  return rotated;
+}
+
 template <typename T>
-static __device__ void svd_onesided_blocked(int m, int n, cplx<T> *C, cplx<T> *V, T *sig2, int *flag,
-                                     double *red, cplx<T> *sbuf, int sbuf_elems) {
+static __device__ bool cross_visit_dispatch(int m, cplx<T> *C, int c0, int wI, int c1, int wJ, T tol, T negligible,
+                                            float *wrk) {
+  if constexpr (sizeof(T) == 4) {
+    return cross_visit_regs<1>(m, C, c0, wI, c1, wJ, tol, negligible, wrk);  // m <= kThreads
+  } else {
+    return false;
+  }
+}
+
+// rv_wrk (kRvWrkFloats floats of shared memory, or null): with it, a
+// complex64 problem without V and with m <= kThreads visits block pairs
+// with cross_visit_regs (blocks of 16 columns); the blocks alone are still
+// staged in shared memory.
+template <typename T>
+static __device__ int svd_onesided_blocked(int m, int n, cplx<T> *C, cplx<T> *V, T *sig2, int *flag,
+                                     double *red, cplx<T> *sbuf, int sbuf_elems, float *rv_wrk = nullptr) {
   const T negligible = onesided_prologue<T>(m, n, C, V, red);
   const T tol = onesided_tol<T>(m);
   // staged block pair: Q (w x w, only with V), norms (w complex slots),
   // columns (m x w)
   const bool withV = V != nullptr;
+  const bool regs = sizeof(T) == 4 && !withV && rv_wrk != nullptr && m <= kThreads &&
+                    static_cast<int64_t>(m) * 16 + 32 <= sbuf_elems;
   int bw = 32;
   while (bw > 1 && static_cast<int64_t>(m) * 2 * bw + (withV ? 4 * bw * bw : 0) + 2 * bw > sbuf_elems) --bw;
   if (bw > 2 * kWarps) bw -= bw % (2 * kWarps);  // whole waves of half warps per step
+  if (regs) bw = 16;
   const int nb = (n + bw - 1) / bw, nbe = nb + (nb & 1);
   const int max_sweeps = sizeof(T) == 4 ? kMaxBlockedSweepsF : kMaxBlockedSweepsD;
   int *any = flag + 1;
@@ -738,6 +936,14 @@ static __device__ void svd_onesided_blocked(int m, int n, cplx<T> *C, cplx<T> *V
     const int c0 = I * bw, wI = min(bw, n - c0);
     const int c1 = J * bw, wJ = self ? 0 : min(bw, n - c1);
     const int w = wI + wJ;
+    if (regs && !self) {
+      if (cross_visit_dispatch<T>(m, C, c0, wI, c1, wJ, tol, negligible, rv_wrk)) {
+        if (skipping && tid() == 0) last_mod[I] = last_mod[J] = stamp;
+        if (tid() == 0) *any = 1;
+      }
+      __syncthreads();
+      return;
+    }
     auto gcol = [&](int c) { return c < wI ? c0 + c : c1 + (c - wI); };
     const int qe = withV ? w * w : 0;
     cplx<T> *Q = withV ? sbuf : nullptr;
@@ -824,7 +1030,9 @@ static __device__ void svd_onesided_blocked(int m, int n, cplx<T> *C, cplx<T> *V
     if (tid() == 0) *any = 1;
   };
 
+  int sweeps = 0;
   for (int sweep = 0; sweep < max_sweeps && n > 1; ++sweep) {
+    ++sweeps;
     if (tid() == 0) *any = 0;
     __syncthreads();
     const int base = sweep * per_sweep;
@@ -845,6 +1053,7 @@ static __device__ void svd_onesided_blocked(int m, int n, cplx<T> *C, cplx<T> *V
     if (!f) break;
   }
   onesided_epilogue<T>(m, n, C, sig2);
+  return sweeps;
 }
 
 // One Newton-Schulz step X <- X (3 I - X^dag X) / 2 on the k orthonormal-to-
@@ -963,7 +1172,7 @@ __host__ __device__ size_t smem_bytes(int n, int W, int svd_elems) {
   add(sizeof(cplx<T>) * svd_elems);  // jbuf
   add(sizeof(cplx<T>) * kMaxVec);     // uvec
   add(sizeof(int) * (n + 2));         // rdim
-  add(sizeof(T) * 512);               // lam
+  add(sizeof(T) * kLamElems);         // lam (also the register-visit reductions)
   add(sizeof(MpoSpec<T>));
   return b;
 }
@@ -993,7 +1202,7 @@ static __device__ Smem<T> carve(char *base, int n, int W, int svd_elems) {
   s.jbuf = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * svd_elems));
   s.uvec = reinterpret_cast<cplx<T> *>(take(sizeof(cplx<T>) * kMaxVec));
   s.rdim = reinterpret_cast<int *>(take(sizeof(int) * (n + 2)));
-  s.lam = reinterpret_cast<T *>(take(sizeof(T) * 512));
+  s.lam = reinterpret_cast<T *>(take(sizeof(T) * kLamElems));
   s.spec = reinterpret_cast<MpoSpec<T> *>(take(sizeof(MpoSpec<T>)));
   return s;
 }
@@ -1043,16 +1252,17 @@ static __device__ Scratch<T> scratch_for(const EngineParams &P, int cap) {
 
 // Algorithmic FLOP counts (real flops of the textbook algorithm, complex = 4
 // real multiply-adds per multiply-add): a GEMM is 8 M N K, a Householder R
-// factor of an m x n matrix 4 (2 m n^2 - 2 n^3 / 3) with m >= n (roles
-// swapped otherwise), the singular values and right vectors of an m x n
-// matrix 4 (4 m n^2 + 8 n^3).
+// factor of an m x n matrix 4 (2 m n^2 - 2 n^3 / 3) with m >= n, the
+// singular values and the vectors of the smaller side of an m x n matrix
+// 4 (4 m n^2 + 8 n^3) with m >= n (roles swapped otherwise in both).
 static __device__ __forceinline__ double gemm_flops(int M, int N, int K) { return 8.0 * M * N * K; }
 static __device__ __forceinline__ double qr_flops(int m, int n) {
   double a = m >= n ? m : n, b = m >= n ? n : m;
   return 4.0 * (2.0 * a * b * b - 2.0 * b * b * b / 3.0);
 }
 static __device__ __forceinline__ double svd_flops(int m, int n) {
-  return 4.0 * (4.0 * m * static_cast<double>(n) * n + 8.0 * static_cast<double>(n) * n * n);
+  double a = m >= n ? m : n, b = m >= n ? n : m;
+  return 4.0 * (4.0 * a * b * b + 8.0 * b * b * b);
 }
 
 // ---------------------------------------------------------------------------
@@ -1390,20 +1600,29 @@ static __device__ void mps_finish(const EngineParams &P, const Smem<T> &S, int64
         __syncthreads();
         return;
       }
+      const long long tqr = clock64();
       qr_r_inplace<T>(r, n2, X.y, n2, S.jbuf, P.svd_elems, S.red, S.dmisc + 4);
+      if (tid() == 0) S.dmisc[D_PROF + 1 + PROF_SVD_QR] += static_cast<double>(clock64() - tqr);
       const int kx = min(r, n2);
-      const bool x_smem = n2 * kx <= P.svd_elems;
+      // complex64 with more than one block of 16 columns: blocked Jacobi
+      // with register-resident block pairs, X in global scratch (L2)
+      const bool regs = sizeof(T) == 4 && kx > 16 && n2 <= kThreads;
+      const bool x_smem = !regs && n2 * kx <= P.svd_elems;
       cplx<T> *Xc = x_smem ? S.jbuf : X.y;
       for (int e = tid(); e < n2 * kx; e += kThreads) Xc[e] = cconj(X.y[e]);
       __syncthreads();
-      if (x_smem) svd_onesided<T>(n2, kx, Xc, nullptr, X.lam, &S.misc[M_JFLAG], S.red);
-      else svd_onesided_blocked<T>(n2, kx, Xc, nullptr, X.lam, &S.misc[M_JFLAG], S.red, S.jbuf, P.svd_elems);
+      const int sweeps =
+          x_smem ? svd_onesided<T>(n2, kx, Xc, nullptr, X.lam, &S.misc[M_JFLAG], S.red)
+                 : svd_onesided_blocked<T>(n2, kx, Xc, nullptr, X.lam, &S.misc[M_JFLAG], S.red, S.jbuf,
+                                           P.svd_elems, regs ? reinterpret_cast<float *>(S.lam) : nullptr);
+      if (tid() == 0) S.dmisc[D_PROF + 1 + PROF_JSWEEPS] += sweeps;
       for (int i = kx + tid(); i < n2; i += kThreads) X.lam[i] = T(0);
       __syncthreads();
       Vc = Xc;
       vec_from_columns = true;
     }
     __syncthreads();
+    if (tid() == 0 && !vec_from_columns) S.dmisc[D_PROF + 1 + PROF_SVD_SMALL] += static_cast<double>(clock64() - tp);
     prof_mark(S.dmisc, PROF_SVD, tp);
     if (tid() == 0) {
       S.dmisc[D_FLOPS] += gemm_flops(r, n2, Dl) + svd_flops(r, n2);
@@ -1684,7 +1903,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
       S.dmisc[D_DISC] = P.disc[shot];
       S.dmisc[D_LOGP] = P.logp[shot];
       S.dmisc[D_FLOPS] = 0.0;
-      for (int i = 0; i < kProfSlots - 1; ++i) S.dmisc[D_PROF + 1 + i] = 0.0;
+      for (int i = 0; i < kProfSlots; ++i) S.dmisc[D_PROF + 1 + i] = 0.0;
     }
     __syncthreads();
     long long t_ops = clock64();
@@ -1860,7 +2079,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
       P.logp[shot] = S.dmisc[D_LOGP];
       P.flops[shot] += S.dmisc[D_FLOPS];
       S.dmisc[D_PROF + 1 + PROF_OPS] = static_cast<double>(clock64() - t_ops);
-      for (int i = 0; i < kProfSlots - 1; ++i) P.prof[shot * kProfSlots + i] += S.dmisc[D_PROF + 1 + i];
+      for (int i = 0; i < kProfSlots; ++i) P.prof[shot * kProfSlots + i] += S.dmisc[D_PROF + 1 + i];
       if (S.misc[M_FAIL]) atomicCAS(P.err, 0, S.misc[M_FAIL]);
     }
     __syncthreads();
@@ -1911,6 +2130,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_check_kernel(int what, int 
   int *flag = reinterpret_cast<int *>(dm + 16);
   cplx<T> *uv = reinterpret_cast<cplx<T> *>(flag + 16);
   cplx<T> *buf = uv + kMaxVec;
+  float *rv_wrk = reinterpret_cast<float *>(buf + SvdSmem<T>::elems);
   if (what == 0) {
     qr_r_inplace<T>(m, n, A, n, buf, SvdSmem<T>::elems, red, dm);
   } else if (what == 2) {
@@ -1923,12 +2143,14 @@ __global__ void __launch_bounds__(kThreads, 1) dense_check_kernel(int what, int 
     // R factor, Jacobi on X = R^dag (n x k), V = normalised columns of X
     qr_r_inplace<T>(m, n, A, n, buf, SvdSmem<T>::elems, red, dm);
     const int k = min(m, n);
-    const bool x_smem = n * k <= SvdSmem<T>::elems;
+    const bool regs = sizeof(T) == 4 && k > 16 && n <= kThreads;
+    const bool x_smem = !regs && n * k <= SvdSmem<T>::elems;
     cplx<T> *Xc = x_smem ? buf : A;
     for (int e = tid(); e < n * k; e += kThreads) Xc[e] = cconj(A[e]);
     __syncthreads();
     if (x_smem) svd_onesided<T>(n, k, Xc, nullptr, sig2, flag, red);
-    else svd_onesided_blocked<T>(n, k, Xc, nullptr, sig2, flag, red, buf, SvdSmem<T>::elems);
+    else svd_onesided_blocked<T>(n, k, Xc, nullptr, sig2, flag, red, buf, SvdSmem<T>::elems,
+                                 regs ? rv_wrk : nullptr);
     for (int e = tid(); e < n * n; e += kThreads) {
       const int c = e / n;
       const T l = c < k ? sig2[c] : T(0);
@@ -1957,6 +2179,7 @@ cudaError_t launch_dense_check_t(int what, int m, int n, void *A, void *V, void 
                                         cudaStream_t s) {
   size_t smem = sizeof(double) * (kThreads + 16) + sizeof(int) * 16 + sizeof(cplx<T>) * kMaxVec;
   smem += sizeof(cplx<T>) * SvdSmem<T>::elems;  // QR panel, SVD matrix or staged column blocks
+  smem += sizeof(float) * kRvWrkFloats;           // register-visit reductions
   cudaError_t e = cudaFuncSetAttribute(dense_check_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;

@@ -27,18 +27,21 @@ __global__ void __launch_bounds__(kThreads, 1) svd_noalloc_kernel(int m, int n, 
   double *dm = red + kThreads;
   int *flag = reinterpret_cast<int *>(dm + 16);
   cplx<T> *buf = reinterpret_cast<cplx<T> *>(flag + 16) + kMaxVec;
+  float *rv_wrk = reinterpret_cast<float *>(buf + SvdSmem<T>::elems);
   for (int e = tid(); e < m * n; e += kThreads) work[e] = C[e];
   __syncthreads();
   // the large-bond path of the truncation sweep on the work copy: R factor,
   // Jacobi on X = R^dag, V = normalised columns of X
   qr_r_inplace<T>(m, n, work, n, buf, SvdSmem<T>::elems, red, dm);
   const int k = min(m, n);
-  const bool x_smem = n * k <= SvdSmem<T>::elems;
+  const bool regs = sizeof(T) == 4 && k > 16 && n <= kThreads;
+  const bool x_smem = !regs && n * k <= SvdSmem<T>::elems;
   cplx<T> *Xc = x_smem ? buf : work;
   for (int e = tid(); e < n * k; e += kThreads) Xc[e] = cconj(work[e]);
   __syncthreads();
   if (x_smem) svd_onesided<T>(n, k, Xc, nullptr, sig2, flag, red);
-  else svd_onesided_blocked<T>(n, k, Xc, nullptr, sig2, flag, red, buf, SvdSmem<T>::elems);
+  else svd_onesided_blocked<T>(n, k, Xc, nullptr, sig2, flag, red, buf, SvdSmem<T>::elems,
+                               regs ? rv_wrk : nullptr);
   for (int e = tid(); e < n * n; e += kThreads) {
     const int c = e / n;
     const T l = c < k ? sig2[c] : T(0);
@@ -78,7 +81,7 @@ static cudaError_t launch_svd_noalloc_t(int m, int n, const void *C, void *V, vo
   cudaError_t e = noalloc_scratch_ptr(&work);
   if (e != cudaSuccess) return e;
   size_t smem = sizeof(double) * (kThreads + 16) + sizeof(int) * 16 + sizeof(cplx<T>) * kMaxVec +
-                sizeof(cplx<T>) * SvdSmem<T>::elems;
+                sizeof(cplx<T>) * SvdSmem<T>::elems + sizeof(float) * kRvWrkFloats;
   e = cudaFuncSetAttribute(svd_noalloc_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem));
   if (e != cudaSuccess) return e;

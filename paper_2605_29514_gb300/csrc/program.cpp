@@ -10,6 +10,10 @@
 //   * crosstalk: every (ancilla, neighbour) edge, gated in one layer, gets
 //     exp(-i theta Z Z) after each of the other three layers; the optional
 //     next-nearest pairs (offset (2,0) or (0,2)) get X X after every layer;
+//     explicit pairs without a layer mask rotate after every layer in which
+//     a CNOT does not act on exactly that pair;
+//   * X-memory: the data qubits get H (with its Eq. 2 noise) after the
+//     initial reset and again before the final Z readout;
 //   * random events numbered in program order (see build_program).
 #include "program.h"
 
@@ -36,13 +40,16 @@ Op make_op(OpKind k, int a, int b, int pauli, int ev, int idx) {
 }
 }  // namespace
 
-std::string build_program(int d, int rounds, int pair_rule, Program &P) {
+std::string build_program(const ProgramSpec &spec, Program &P) {
+  const int d = spec.d, rounds = spec.rounds, pair_rule = spec.pair_rule;
   if (d < 3 || d % 2 == 0 || d > 11) return "distance must be odd, 3..11";
   if (rounds < 1 || rounds > 1000) return "rounds must be 1..1000";
   if (pair_rule != 0 && pair_rule != 1) return "unknown pair_rule";
+  if (spec.basis != 0 && spec.basis != 1) return "memory_basis must be 0 (Z) or 1 (X)";
   P = Program();
   P.d = d;
   P.rounds = rounds;
+  P.basis = spec.basis;
 
   // (y, x, kind) of every qubit, sorted row-major.
   std::vector<std::tuple<int, int, char>> pts;
@@ -82,13 +89,55 @@ std::string build_program(int d, int rounds, int pair_rule, Program &P) {
     for (int l = 0; l < 4; ++l)
       P.slots[4 * ai + l] = at(P.xy[2 * a] + ord[l][0], P.xy[2 * a + 1] + ord[l][1]);
   }
+  if (!spec.schedule.empty()) {
+    // a caller's schedule: each ancilla gates each of its face's data
+    // qubits in exactly one layer, no qubit twice in one layer
+    if (spec.schedule.size() != P.slots.size()) return "cnot_schedule needs 4 entries per ancilla";
+    std::vector<std::vector<char>> busy(4, std::vector<char>(P.n, 0));
+    for (size_t ai = 0; ai < P.anc.size(); ++ai) {
+      std::vector<int> face, got;
+      for (int l = 0; l < 4; ++l) {
+        if (P.slots[4 * ai + l] >= 0) face.push_back(P.slots[4 * ai + l]);
+        const int q = spec.schedule[4 * ai + l];
+        if (q < -1 || q >= P.n) return "cnot_schedule entry out of range";
+        if (q >= 0) got.push_back(q);
+      }
+      std::sort(face.begin(), face.end());
+      std::sort(got.begin(), got.end());
+      if (face != got) return "cnot_schedule: an ancilla must gate each of its data qubits once";
+      for (int l = 0; l < 4; ++l) {
+        const int q = spec.schedule[4 * ai + l];
+        if (q < 0) continue;
+        if (busy[l][q] || busy[l][P.anc[ai]]) return "cnot_schedule: a qubit is gated twice in one layer";
+        busy[l][q] = busy[l][P.anc[ai]] = 1;
+      }
+    }
+    P.slots = spec.schedule;
+  }
 
   // Crosstalk pairs.
-  for (size_t ai = 0; ai < P.anc.size(); ++ai)
-    for (int l = 0; l < 4; ++l)
-      if (P.slots[4 * ai + l] >= 0)
-        P.pairs.push_back({P.anc[ai], P.slots[4 * ai + l], 0, 0xF & ~(1 << l)});
-  if (pair_rule == 1) {
+  if (spec.explicit_pairs) {
+    for (const Pair &p : spec.pairs) {
+      if (p.a < 0 || p.b < 0 || p.a >= P.n || p.b >= P.n || p.a == p.b) return "pair qubit out of range";
+      if (p.pauli != 0 && p.pauli != 1) return "pair_pauli must be 0 (ZZ) or 1 (XX)";
+      int mask = p.layer_mask;
+      if (mask < 0) {  // idle rule: every layer in which no CNOT acts on exactly this pair
+        mask = 0xF;
+        for (size_t ai = 0; ai < P.anc.size(); ++ai)
+          for (int l = 0; l < 4; ++l) {
+            const int a = P.anc[ai], q = P.slots[4 * ai + l];
+            if (q >= 0 && ((a == p.a && q == p.b) || (a == p.b && q == p.a))) mask &= ~(1 << l);
+          }
+      }
+      P.pairs.push_back({p.a, p.b, p.pauli, mask & 0xF});
+    }
+  } else {
+    for (size_t ai = 0; ai < P.anc.size(); ++ai)
+      for (int l = 0; l < 4; ++l)
+        if (P.slots[4 * ai + l] >= 0)
+          P.pairs.push_back({P.anc[ai], P.slots[4 * ai + l], 0, 0xF & ~(1 << l)});
+  }
+  if (!spec.explicit_pairs && pair_rule == 1) {
     for (int q = 0; q < P.n; ++q) {
       const int off[2][2] = {{2, 0}, {0, 2}};
       for (auto &o : off) {
@@ -102,6 +151,12 @@ std::string build_program(int d, int rounds, int pair_rule, Program &P) {
   int ev = 0, rec = 0;
   P.seg_begin.push_back(0);
   for (int q = 0; q < P.n; ++q) P.ops.push_back(make_op(OP_RESET_FLIP, q, 0, 0, ev++, 0));
+  if (P.basis == 1) {  // X-memory: data qubits start in |+>
+    for (int q : P.data) {
+      P.ops.push_back(make_op(OP_H, q, 0, 0, 0, 0));
+      P.ops.push_back(make_op(OP_NOISE1, q, 0, 0, ev++, 0));
+    }
+  }
   std::vector<int> xanc;
   for (int a : P.anc)
     if (P.kind[a] == 'X') xanc.push_back(a);
@@ -135,6 +190,12 @@ std::string build_program(int d, int rounds, int pair_rule, Program &P) {
     }
   }
   P.seg_begin.push_back(static_cast<int>(P.ops.size()));
+  if (P.basis == 1) {  // X readout: H, then the Z measurement
+    for (int q : P.data) {
+      P.ops.push_back(make_op(OP_H, q, 0, 0, 0, 0));
+      P.ops.push_back(make_op(OP_NOISE1, q, 0, 0, ev++, 0));
+    }
+  }
   for (int q : P.data) {
     P.ops.push_back(make_op(OP_MEAS, q, 0, 0, ev, rec++));
     ev += 2;
@@ -143,10 +204,12 @@ std::string build_program(int d, int rounds, int pair_rule, Program &P) {
   P.n_events = ev;
   P.n_meas = rec;
 
-  // Detectors (Sec. II): round 0 sees only the Z faces, which start in a
-  // definite state; from round 1 on every face is compared with its previous
-  // outcome; the final data readout closes each Z face with its last round.
+  // Detectors (Sec. II) of a memory experiment in basis B: round 0 sees only
+  // the B faces, which start in a definite state; from round 1 on every face
+  // is compared with its previous outcome; the final data readout closes
+  // each B face with its last round.
   const int na = static_cast<int>(P.anc.size());
+  const char bkind = P.basis == 1 ? 'X' : 'Z';
   auto add_det = [&](std::initializer_list<int> idx, const std::vector<int> &more) {
     int k = 0;
     for (int i : idx) P.det.push_back(i), ++k;
@@ -158,7 +221,7 @@ std::string build_program(int d, int rounds, int pair_rule, Program &P) {
   for (int r = 0; r < rounds; ++r)
     for (int ai = 0; ai < na; ++ai) {
       if (r == 0) {
-        if (P.kind[P.anc[ai]] == 'Z') add_det({ai}, none);
+        if (P.kind[P.anc[ai]] == bkind) add_det({ai}, none);
       } else {
         add_det({r * na + ai, (r - 1) * na + ai}, none);
       }
@@ -166,15 +229,16 @@ std::string build_program(int d, int rounds, int pair_rule, Program &P) {
   std::vector<int> data_pos(P.n, -1);
   for (size_t i = 0; i < P.data.size(); ++i) data_pos[P.data[i]] = rounds * na + static_cast<int>(i);
   for (int ai = 0; ai < na; ++ai) {
-    if (P.kind[P.anc[ai]] != 'Z') continue;
+    if (P.kind[P.anc[ai]] != bkind) continue;
     std::vector<int> dq;
     for (int l = 0; l < 4; ++l)
       if (P.slots[4 * ai + l] >= 0) dq.push_back(data_pos[P.slots[4 * ai + l]]);
     add_det({(rounds - 1) * na + ai}, dq);
   }
-  // Z_L: the data qubits of the top row (y = 1)
+  // Z_L: the data qubits of the top row (y = 1); X_L: the left column (x = 1)
   for (int q : P.data)
-    if (P.xy[2 * q + 1] == 1) P.logical.push_back(data_pos[q]);
+    if ((P.basis == 0 && P.xy[2 * q + 1] == 1) || (P.basis == 1 && P.xy[2 * q] == 1))
+      P.logical.push_back(data_pos[q]);
   return std::string();
 }
 

@@ -33,8 +33,20 @@ struct Pair {
   int32_t a, b, pauli, layer_mask;
 };
 
+// What the caller asks for (stn_config, deep-copied): code distance and
+// rounds, memory basis (0 Z, 1 X), an optional CNOT schedule ([n_anc][4]
+// data qubits or -1, ancillas in ascending qubit order; empty = the default
+// order) and optional explicit crosstalk pairs (layer_mask < 0: the layers in
+// which the pair is not gated; empty with explicit_pairs false = pair_rule).
+struct ProgramSpec {
+  int d = 0, rounds = 0, pair_rule = 0, basis = 0;
+  std::vector<int32_t> schedule;
+  bool explicit_pairs = false;
+  std::vector<Pair> pairs;
+};
+
 struct Program {
-  int d = 0, rounds = 0, n = 0;
+  int d = 0, rounds = 0, n = 0, basis = 0;
   std::vector<int> xy;          // qubit -> x, y (2 ints)
   std::vector<int> data, anc;   // qubit indices
   std::vector<char> kind;       // qubit -> 'D', 'X', 'Z'
@@ -53,6 +65,6 @@ struct Program {
 constexpr int kDetWidth = 6;
 
 // Builds the program; returns an empty string or the reason for failure.
-std::string build_program(int d, int rounds, int pair_rule, Program &out);
+std::string build_program(const ProgramSpec &spec, Program &out);
 
 }  // namespace stn

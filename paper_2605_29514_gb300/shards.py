@@ -29,6 +29,19 @@ def rank_base(rank):
     return rank * RANK_STRIDE
 
 
+def batch_offset(rank, batch, shots_per_batch):
+    """First global shot index of batch number `batch` (0, 1, ...) of `rank`
+    in a weak-scaling run whose batches hold `shots_per_batch` shots: the
+    batches of one rank are consecutive ranges starting at rank_base(rank),
+    so ranks never share a shot as long as a rank runs fewer than
+    RANK_STRIDE shots."""
+    if rank < 0 or batch < 0 or shots_per_batch < 1:
+        raise ValueError("bad batch request")
+    if (batch + 1) * shots_per_batch > RANK_STRIDE:
+        raise ValueError("a rank's shots would reach the next rank's range")
+    return rank_base(rank) + batch * shots_per_batch
+
+
 def allreduce_sum(arrays, dist=None, device="cpu"):
     """Element-wise sum of each numpy array over all ranks; returns the
     summed arrays.  Without an initialised process group this is the

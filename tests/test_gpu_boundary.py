@@ -1,0 +1,91 @@
+"""The boundary's problem statement and failure paths on the GPU, through the
+C ABI: explicit crosstalk pairs equal to the default rule give the default
+run bit for bit; X-memory and a caller's CNOT schedule match the oracle;
+an arena too small for a sweep and a non-finite angle come back as statuses,
+and the context stays usable."""
+
+import numpy as np
+import pytest
+
+import paper_2605_29514_gb300 as stn
+from oracle.circuit import build_layout, build_pairs, detectors, logical_z
+from oracle.shot import make_program, run_shot
+from test_gpu_parity import compare_shot, gpu_run
+from test_oracle_shot import transposed_schedule
+from workloads import D3_EXACT, theta_table
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    stn.build()
+
+
+def test_explicit_default_pairs_reproduce_records_bit_for_bit():
+    rule = build_pairs(build_layout(3), "adjacent_idle")
+    w = D3_EXACT.with_(p=0.02, rounds=2)
+    shots = 8
+    _, base, theta = gpu_run(w, shots)
+    for masks in (True, False):
+        we = w.with_(pairs=tuple((p.a, p.b, p.pauli, p.layer_mask if masks else None) for p in rule))
+        _, out, _ = gpu_run(we, shots, theta=theta)
+        assert np.array_equal(out["records"], base["records"])
+        assert np.array_equal(out["born"], base["born"])
+
+
+@pytest.mark.parametrize("variant", ["x_memory", "schedule_pairs_x_memory"])
+def test_problem_statement_parity(variant):
+    """X-memory (data prepared and read out in X), alone and with the
+    transposed CNOT schedule and explicit pairs (a subset with the idle rule
+    plus one XX pair on fixed layers): records, Born probabilities (1e-11),
+    tableaux, and the device's detectors and X_L against the oracle."""
+    w = D3_EXACT.with_(rounds=2, p=0.02, memory_basis="X")
+    if variant == "schedule_pairs_x_memory":
+        lay = build_layout(3)
+        rule = build_pairs(lay, "adjacent_idle")
+        pairs = tuple((p.a, p.b, p.pauli, None) for p in rule[::3]) + ((lay.data[0], lay.data[1], "XX", 0b0101),)
+        w = w.with_(cnot_schedule=transposed_schedule(3), pairs=pairs)
+    shots = 8
+    sim, out, theta = gpu_run(w, shots)
+    prog = make_program(w)
+    det, obs = sim.read_detectors()
+    for s in range(shots):
+        ref = run_shot(w, s, theta, prog)
+        assert compare_shot(sim, out, s, ref, 1e-11)
+        rec = list(out["bits"][s])
+        assert list(det[s]) == detectors(prog, rec)
+        assert int(obs[s]) == logical_z(prog, rec)
+
+
+def test_arena_cap_overflow_is_reported():
+    """A per-shot span arena capped below what a sweep needs stops the shots
+    with STN_EOVERFLOW through stn_sample_shots; the same context then runs a
+    batch that fits (theta = 0 keeps every bond at 1)."""
+    w = D3_EXACT.with_(rounds=1)
+    sim = stn.Simulator(w, max_shots=4, arena_cap_bytes=8192)
+    theta = theta_table(w, sim.n_pairs)
+    with pytest.raises(stn.StnError) as e:
+        sim.sample_shots(4, 0, theta)
+    assert e.value.status == stn.STN_EOVERFLOW
+    out = sim.sample_shots(4, 0, np.zeros_like(theta))
+    assert np.all(out["max_chi"] == 1)
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+def test_non_finite_theta_rejected(bad):
+    w = D3_EXACT.with_(rounds=1)
+    sim = stn.Simulator(w, max_shots=2)
+    theta = theta_table(w, sim.n_pairs)
+    theta[3] = bad
+    with pytest.raises(stn.StnError) as e:
+        sim.sample_shots(2, 0, theta)
+    assert e.value.status == stn.STN_EINVAL
+    theta[3] = 0.05
+    out = sim.sample_shots(2, 0, theta)
+    ref = run_shot(w, 1, theta)
+    assert list(out["bits"][1]) == ref.record

@@ -1,0 +1,93 @@
+"""Whole shots of the benchmark workload (d=5, 5 rounds, theta = 0.10,
+p = 1e-3, chi cap 256, complex64 contractions) on the GPU against the
+oracle's stored records (tests/golden/oracle_d5_records.txt, written by
+make_oracle_d5_golden.py from oracle/ alone).
+
+Bars: Born probabilities of the realised outcomes within 1e-5 relative
+(floor 1e-4 in the denominator); records identical except after a Born draw
+within 1e-5 of its threshold (counted on either side); the largest bond and
+log P agree.  The same GPU shot is also compared with the oracle run at its
+own complex128 cutoff (1e-12) and the error is reported."""
+
+import os
+
+import numpy as np
+import pytest
+
+import paper_2605_29514_gb300 as stn
+from workloads import D5_BENCH, theta_table
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def load_golden(name):
+    rows, meta = {}, {}
+    path = os.path.join(HERE, name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not generated")
+    for line in open(path):
+        if line.startswith("# shot"):
+            f = line.split()
+            shot = int(f[2].rstrip(":"))
+            kv = dict(zip(f[3::2], f[4::2]))
+            meta[shot] = {k: float(v) for k, v in kv.items()}
+        elif not line.startswith("#") and line.strip():
+            f = line.split()
+            rows[int(f[0])] = ([int(c) for c in f[1]], np.array([float(x) for x in f[2:]]))
+    return rows, meta
+
+
+@pytest.fixture(scope="module")
+def gpu_shots():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    stn.build()
+    rows, meta = load_golden("oracle_d5_records.txt")
+    shots = max(rows) + 1
+    sim = stn.Simulator(D5_BENCH, max_shots=shots)
+    out = sim.sample_shots(shots, 0, theta_table(D5_BENCH, sim.n_pairs))
+    sim.close()
+    return out, rows, meta
+
+
+def first_divergence(bits, rec):
+    return next((i for i in range(len(rec)) if bits[i] != rec[i]), None)
+
+
+def test_whole_d5_shots_match_oracle(gpu_shots):
+    out, rows, meta = gpu_shots
+    worst = 0.0
+    for s, (rec, born) in rows.items():
+        bits = list(out["bits"][s])
+        div = first_divergence(bits, rec)
+        upto = len(rec) if div is None else div
+        if div is not None:
+            assert out["near_draws"][s] > 0 or meta[s]["near_draws"] > 0, f"shot {s}: record {div} differs"
+        err = np.abs(out["born"][s][:upto] - born[:upto]) / np.maximum(born[:upto], 1e-4)
+        worst = max(worst, float(err.max()))
+        assert np.all(err < 1e-5), f"shot {s}: max rel Born error {err.max():.3e} at record {int(err.argmax())}"
+        if div is None:
+            assert out["max_chi"][s] == meta[s]["max_chi"]
+            assert abs(out["logp"][s] - meta[s]["logp"]) < 1e-4 * max(1.0, abs(meta[s]["logp"]))
+    print(f"max relative Born error over {len(rows)} whole shots: {worst:.3e}")
+
+
+def test_d5_shot_against_tight_cutoff_oracle(gpu_shots):
+    """The complex64 path (cutoff 5e-6) against the oracle at cutoff 1e-12:
+    the error of the whole approximation, stated, with records identical up
+    to near-threshold draws and Born probabilities within 1e-3 relative."""
+    out, _, _ = gpu_shots
+    rows, meta = load_golden("oracle_d5_records_cut1e-12.txt")
+    for s, (rec, born) in rows.items():
+        bits = list(out["bits"][s])
+        div = first_divergence(bits, rec)
+        upto = len(rec) if div is None else div
+        err = np.abs(out["born"][s][:upto] - born[:upto]) / np.maximum(born[:upto], 1e-4)
+        print(f"shot {s} vs the 1e-12-cutoff oracle: records agree through {upto} of {len(rec)}, "
+              f"max relative Born error {err.max():.3e}")
+        if div is not None:
+            assert out["near_draws"][s] > 0 or meta[s]["near_draws"] > 0
+        assert np.all(err < 1e-3)

@@ -85,3 +85,56 @@ def test_sharded_tallies_equal_single_process():
     assert np.array_equal(np.array(det), det1)
     assert misc[0] == misc1[0] and misc[2] == total
     assert abs(misc[1] - misc1[1]) < 1e-9 * max(1.0, abs(misc1[1]))
+
+
+def test_batch_offsets_disjoint_within_and_across_ranks():
+    from paper_2605_29514_gb300.shards import RANK_STRIDE, batch_offset
+    B = 152
+    ranges = []
+    for rank in range(4):
+        for b in range(30):
+            lo = batch_offset(rank, b, B)
+            ranges.append((lo, lo + B))
+    ranges.sort()
+    for (lo0, hi0), (lo1, _) in zip(ranges, ranges[1:]):
+        assert hi0 <= lo1
+    with pytest.raises(ValueError):
+        batch_offset(0, RANK_STRIDE // B, B)
+
+
+def _offset_worker(rank, world, port, q):
+    import torch.distributed as dist
+    from paper_2605_29514_gb300.shards import batch_offset
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # the warm-up and timed batches of bench.py on this rank: W + K/6 batches of 152
+    mine = torch.tensor([batch_offset(rank, b, 152) for b in range(8)], dtype=torch.int64)
+    got = [torch.zeros_like(mine) for _ in range(world)]
+    dist.all_gather(got, mine)
+    if rank == 0:
+        q.put([g.tolist() for g in got])
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_bench_batch_offsets_on_cpu_ranks():
+    """Each rank of a two-rank gloo job computes the global shot offsets of its
+    batches as bench.py does; gathered on rank 0 the shot ranges are
+    pairwise disjoint."""
+    import multiprocessing as mp
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_offset_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    offsets = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    spans = sorted((lo, lo + 152) for per_rank in offsets for lo in per_rank)
+    assert len(spans) == 16
+    for (lo0, hi0), (lo1, _) in zip(spans, spans[1:]):
+        assert hi0 <= lo1

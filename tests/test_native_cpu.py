@@ -106,3 +106,75 @@ def test_detector_table_matches_oracle(lib, w):
         got = np.bitwise_xor.reduce(ext[det], axis=1)
         assert list(got) == detectors(prog, list(rec))
         assert int(np.bitwise_xor.reduce(rec[logical])) == logical_z(prog, list(rec))
+
+
+def _schedule_and_pairs():
+    from test_oracle_shot import transposed_schedule
+    from oracle.circuit import build_layout, build_pairs
+    lay = build_layout(3)
+    rule = build_pairs(lay, "adjacent_idle")
+    pairs = tuple((p.a, p.b, p.pauli, None) for p in rule[::3]) + ((lay.data[0], lay.data[1], "XX", None),)
+    return transposed_schedule(3), pairs, rule
+
+
+@pytest.mark.parametrize("variant", ["x_memory", "schedule", "pairs_idle_rule", "pairs_masks", "all"])
+def test_problem_statement_fields_compile_like_the_oracle(lib, variant):
+    """The boundary's problem statement (memory basis, CNOT schedule, explicit
+    pairs with or without layer masks) compiles to the oracle's program, pairs
+    and detector table."""
+    from oracle.circuit import detectors, logical_z
+    schedule, pairs, rule = _schedule_and_pairs()
+    w = D3_EXACT.with_(rounds=2, p=0.01)
+    if variant in ("x_memory", "all"):
+        w = w.with_(memory_basis="X")
+    if variant in ("schedule", "all"):
+        w = w.with_(cnot_schedule=schedule)
+    if variant in ("pairs_idle_rule", "all"):
+        w = w.with_(pairs=pairs)
+    if variant == "pairs_masks":
+        w = w.with_(pairs=tuple((p.a, p.b, "XX" if k % 5 == 0 else "ZZ", (k * 7) % 16)
+                                for k, p in enumerate(rule)))
+    counts, ops, got_pairs = stn.compile_program(w)
+    prog = make_program(w)
+    assert counts[3] == prog.n_events and counts[2] == prog.n_meas
+    rows = oracle_rows(prog)
+    assert np.array_equal(ops, rows)
+    ref_pairs = np.array([[p.a, p.b, 0 if p.pauli == "ZZ" else 1, p.layer_mask] for p in prog.pairs])
+    assert np.array_equal(got_pairs, ref_pairs)
+    det, logical = stn.compile_detectors(w)
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        rec = rng.integers(0, 2, size=w.n_meas)
+        ext = np.append(rec, 0)
+        assert list(np.bitwise_xor.reduce(ext[det], axis=1)) == detectors(prog, list(rec))
+        assert int(np.bitwise_xor.reduce(rec[logical])) == logical_z(prog, list(rec))
+
+
+def test_explicit_default_pairs_give_the_default_program(lib):
+    _, _, rule = _schedule_and_pairs()
+    base = stn.compile_program(D3_EXACT)
+    for masks in (True, False):
+        w = D3_EXACT.with_(pairs=tuple((p.a, p.b, p.pauli, p.layer_mask if masks else None) for p in rule))
+        got = stn.compile_program(w)
+        assert all(np.array_equal(x, y) for x, y in zip(got, base))
+
+
+def test_invalid_schedule_and_pairs_rejected(lib):
+    schedule, pairs, _ = _schedule_and_pairs()
+    bad_schedule = [list(r) for r in schedule]
+    bad_schedule[0] = [bad_schedule[0][0]] * 4
+    for w in (D3_EXACT.with_(cnot_schedule=tuple(map(tuple, bad_schedule))),
+              D3_EXACT.with_(pairs=((0, 0, "ZZ", None),)),
+              D3_EXACT.with_(pairs=((0, 99, "ZZ", None),))):
+        with pytest.raises(stn.StnError) as e:
+            stn.compile_program(w)
+        assert e.value.status == stn.STN_EINVAL
+
+
+def test_layout_entry_point(lib):
+    from oracle.circuit import build_layout
+    for d in (3, 5):
+        xy, kind = stn.layout(d)
+        lay = build_layout(d)
+        assert [tuple(v) for v in xy] == lay.coords
+        assert [k for k in kind] == ["D" if q in lay.data else lay.kind[q] for q in range(lay.n)]

@@ -276,3 +276,104 @@ def test_planted_mistakes_are_caught(monkeypatch):
         with monkeypatch.context() as m:
             m.setattr(owner, name, fn)
             assert _some_pin_fails(), name
+
+
+# -- the caller's problem statement: memory basis, CNOT schedule, pairs --------
+def transposed_schedule(d):
+    """Z faces take the X faces' default order and vice versa (NW, NE, SW, SE
+    for Z; NW, SW, NE, SE for X): the other hook-respecting choice, in which
+    the X and Z checks sharing two data qubits still meet them in the same
+    relative order."""
+    lay = build_layout(d)
+    rows = []
+    for a in lay.ancillas:
+        x, y = lay.coords[a]
+        order = oc.Z_ORDER if lay.kind[a] == "X" else oc.X_ORDER
+        rows.append(tuple(lay.index.get((x + dx, y + dy), -1) for dx, dy in order))
+    return tuple(rows)
+
+
+@pytest.mark.parametrize("d", [3, 5])
+def test_x_memory_theta_zero_detectors_vanish(d):
+    """X-memory (data prepared and read out in X): at theta = 0 without noise
+    every X-face detector and the X_L parity are deterministic zeros."""
+    w = D3_EXACT.with_(distance=d, rounds=2, theta=0.0, p=0.0, memory_basis="X")
+    prog = make_program(w)
+    assert prog.basis == "X"
+    for shot in range(3):
+        r = run_shot(w, shot, program=prog)
+        assert r.max_chi == 1
+        assert all(b == 0 for b in detectors(prog, r.record))
+        assert logical_z(prog, r.record) == 0
+
+
+def test_transposed_schedule_theta_zero_detectors_vanish():
+    w = D3_EXACT.with_(rounds=2, theta=0.0, p=0.0, cnot_schedule=transposed_schedule(3))
+    prog = make_program(w)
+    assert prog.layout.slots != build_layout(3).slots
+    for shot in range(3):
+        r = run_shot(w, shot, program=prog)
+        assert all(b == 0 for b in detectors(prog, r.record))
+
+
+def test_invalid_schedules_rejected():
+    import itertools
+    good = [list(r) for r in transposed_schedule(3)]
+    build_layout(3, good)
+    twice = [list(r) for r in good]
+    twice[0] = [twice[0][0], twice[0][0], -1, -1]  # one data qubit twice, one never
+    with pytest.raises(ValueError):
+        build_layout(3, twice)
+    with pytest.raises(ValueError):
+        build_layout(3, good[:-1])
+    # a permutation of one weight-4 ancilla's layers that gates a data qubit
+    # in a layer where another ancilla already gates it
+    lay = build_layout(3)
+    i = next(k for k, a in enumerate(lay.ancillas) if all(q is not None for q in lay.slots[a]))
+    clashes = 0
+    for perm in itertools.permutations(good[i]):
+        trial = [list(r) for r in good]
+        trial[i] = list(perm)
+        try:
+            build_layout(3, trial)
+        except ValueError:
+            clashes += 1
+    assert clashes > 0
+
+
+def test_explicit_pairs_reproduce_the_rule():
+    """The default pairs given explicitly, with their masks or with none (the
+    idle rule), compile to the same program and the same records."""
+    lay = build_layout(3)
+    rule = build_pairs(lay, "adjacent_idle")
+    with_masks = tuple((p.a, p.b, p.pauli, p.layer_mask) for p in rule)
+    idle = tuple((p.a, p.b, p.pauli, None) for p in rule)
+    w = D3_EXACT.with_(rounds=2, p=0.01)
+    base = make_program(w)
+    for explicit in (with_masks, idle):
+        prog = make_program(w.with_(pairs=explicit))
+        assert prog.ops == base.ops
+        assert [(p.a, p.b, p.pauli, p.layer_mask) for p in prog.pairs] == \
+            [(p.a, p.b, p.pauli, p.layer_mask) for p in base.pairs]
+    th = theta_table(w, len(base.pairs))
+    r0 = run_shot(w, 1, th, base)
+    r1 = run_shot(w.with_(pairs=idle), 1, th)
+    assert r0.record == r1.record and r0.born == r1.born
+
+
+def test_x_memory_and_schedule_match_dense_statevector():
+    """X-memory with the transposed schedule and explicit pairs (a subset with
+    a mixed layer pattern, one XX pair), with noise: the oracle agrees with the
+    dense statevector of the same program."""
+    lay = build_layout(3)
+    rule = build_pairs(lay, "adjacent_idle")
+    pairs = tuple((p.a, p.b, p.pauli, None) for p in rule[::3]) + ((lay.data[0], lay.data[1], "XX", 0b0101),)
+    w = D3_EXACT.with_(rounds=2, chi_cap=256, p=0.02, theta=0.09, svd_cutoff=1e-14, degeneracy_tol=0.0,
+                       memory_basis="X", cnot_schedule=transposed_schedule(3), pairs=pairs)
+    prog = make_program(w)
+    th = theta_table(w.with_(theta_sigma=0.03), len(prog.pairs))
+    for shot in range(2):
+        rec, born = run_dense(w, prog, th, shot)
+        r = run_shot(w, shot, th, prog)
+        assert r.record == rec
+        assert np.max(np.abs(np.array(born) - np.array(r.born))) < 1e-11

@@ -14,7 +14,10 @@ torch = pytest.importorskip("torch")
 CDT = {0: torch.complex128, 1: torch.complex64}
 RDT = {0: torch.float64, 1: torch.float32}
 TOL = {0: 1e-12, 1: 2e-5}
-SIZES = {0: [(128, 256), (200, 96)], 1: [(256, 256), (300, 200)]}  # within the 1 MiB scratch
+# Within the 1 MiB scratch: shapes whose R^dag fits shared memory (complex128
+# 64 x 64, complex64 16 x 64: the unblocked Jacobi), blocked shapes, and one
+# request of exactly 1 MiB (complex128 256 x 256, complex64 512 x 256).
+SIZES = {0: [(64, 64), (128, 256), (200, 96), (256, 256)], 1: [(16, 64), (256, 256), (300, 200), (512, 256)]}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -50,6 +53,10 @@ def test_noalloc_matches_allocating_entry_point(precision):
         g2 = s2.cpu().numpy().astype(np.float64)
         smax = g2.max()
         assert np.abs(g1 - g2).max() <= TOL[precision] * smax
+        # and both against LAPACK: the singular values of the input
+        s_ref = np.linalg.svd(a, compute_uv=False)
+        got = np.sort(np.sqrt(np.maximum(g1, 0)))[::-1][: len(s_ref)]
+        assert np.abs(got - s_ref).max() <= TOL[precision] * 10 * s_ref[0]
         # right vectors of the well-separated leading values agree
         lead = np.argsort(-g2)[:16]
         x1 = v1.cpu().numpy().T.astype(np.complex128)[:, lead]
@@ -62,3 +69,6 @@ def test_noalloc_rejects_oversize():
     with pytest.raises(stn.StnError) as err:
         stn.dense_svd_noalloc(1, 1024, 256, big.data_ptr(), big.data_ptr(), big.data_ptr())
     assert err.value.status == 7  # STN_EOVERFLOW: beyond the 1 MiB scratch, nothing launched
+    with pytest.raises(stn.StnError) as err:
+        stn.dense_svd_noalloc(1, 1, 10000, big.data_ptr(), big.data_ptr(), big.data_ptr())
+    assert err.value.status == 1  # STN_EINVAL: n beyond 512, nothing launched

@@ -42,6 +42,13 @@ class Workload:
     pair_rule: str = "adjacent_idle"
     theta_sigma: float = 0.0
     theta_seed: int = 7
+    # Z or X memory; optional caller CNOT schedule (one 4-tuple of data
+    # qubits or -1 per ancilla, ancillas in ascending qubit order) and
+    # explicit crosstalk pairs ((a, b, 'ZZ' | 'XX', layer mask or None), in
+    # place of pair_rule).
+    memory_basis: str = "Z"
+    cnot_schedule: tuple = None
+    pairs: tuple = None
 
     def with_(self, **kw):
         return replace(self, **kw)
