@@ -2,21 +2,25 @@
 on one GB300 (theta = 0.10 ZZ on idle adjacent pairs, depolarising p = 1e-3
 with the Table I ratios, chi cap 256, complex64 contractions).
 
-A step is one program segment (a syndrome round, or the final data readout)
-applied to a batch of B shots, one launch of the persistent round kernel; a
-batch is complete after rounds + 1 = 6 steps and the next batch starts with
-new global shot indices.  Exactly K steps are timed, starting with segment 0
+A step is one layer step of the program (stn_apply_step_device) applied to a
+batch of B shots, one launch of the persistent round kernel: CNOT layer l of
+syndrome round r with the crosstalk rotations after it, the round's opening
+H gates in its first layer and its closing H gates and ancilla measurements
+in its last, the final data readout in the very last step.  A batch is
+complete after 4 x rounds = 20 steps, and the next batch starts with new
+global shot indices.  Exactly K steps are timed, starting with the first step
 of a fresh batch, and
 
     value = shots of the batches completed in the timed region / seconds
 
 (CUDA events on the simulator's stream, angles and program resident in HBM).
-The steps of a batch left incomplete at the end of the timed region are
-timed but their shots are not counted, so the value is conservative.  The W
-warm-up steps are syndrome round 0 of W fresh batches.  `e2e` is the same
-steps timed on the host clock through the C ABI with host buffers: the angle
-upload from pinned memory and every completed batch's record download into
-pinned memory are inside it.
+With K = 20 the timed region is exactly one whole batch of 5-round shots.
+Steps of a batch left incomplete at the end of the timed region are timed
+but their shots are not counted, so the value is conservative.  The W warm-up
+steps are the first W steps of a warm-up batch.  `e2e` is the same steps
+timed on the host clock through the C ABI with host buffers: the angle upload
+from pinned memory and every completed batch's record download into pinned
+memory are inside it.
 
 Run: python bench.py [--gpus N] [--steps K] [--warmup W] [--shots B]
      python bench.py --impl reference      (the CPU oracle, bounded sample)
@@ -47,7 +51,7 @@ GOLDEN_D5 = os.path.join(ROOT, "tests", "golden", "oracle_d5_records.txt")
 def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--shots", type=int, default=0, help="shots per batch and rank (default: one per SM)")
     ap.add_argument("--impl", default="stn", choices=["stn", "reference"])
@@ -356,7 +360,6 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
     stn.build()
-    segs = w.rounds + 1
     K = max(1, args.steps)
     W = max(3, args.warmup)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -369,13 +372,17 @@ def main():
     d_theta = torch.empty_like(th_host, device="cuda")
     d_theta.copy_(th_host)
     rec_host = torch.empty((B, sim.rec_bytes), dtype=torch.uint8).pin_memory()
+    segs = sim.n_steps  # layer steps per batch
     plan, complete = timed_plan(K, segs)
 
-    # warm-up: W steps, each the first segment (syndrome round 0) of a fresh batch
+    # warm-up: the first W steps of a warm-up batch (wrapping into new batches)
     for i in range(W):
-        sim.begin_batch(B, batch_offset(rank, i, B))
-        sim.apply_round_device(0, d_theta.data_ptr())
+        b, g = divmod(i, segs)
+        if g == 0:
+            sim.begin_batch(B, batch_offset(rank, b, B))
+        sim.apply_step_device(g, d_theta.data_ptr())
     sim.sync()
+    first_timed_batch = (W + segs - 1) // segs
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
@@ -392,10 +399,10 @@ def main():
     ev0.record(stream)
     for i, (b, g) in enumerate(plan):
         if g == 0:
-            sim.begin_batch(B, batch_offset(rank, W + b, B))
+            sim.begin_batch(B, batch_offset(rank, first_timed_batch + b, B))
             launches += 1
         kev[i][0].record(stream)
-        sim.apply_round_device(g, d_theta.data_ptr())
+        sim.apply_step_device(g, d_theta.data_ptr())
         kev[i][1].record(stream)
         launches += 1
         if g == segs - 1:
@@ -416,13 +423,15 @@ def main():
     dprof = {k: prof1[k] - prof0[k] for k in prof1}
     loop = max(dprof["op_loop_cycles"], 1.0)
     shot_segs = max(1, B * K)
-    phases = {"segment_ms": {str(g): round(statistics.mean(v), 1) for g, v in sorted(seg_ms.items())},
+    phases = {"step_ms": {str(g): round(statistics.mean(v), 1) for g, v in sorted(seg_ms.items())},
               "cycle_share": {k.replace("_cycles", ""): round(dprof[k] / loop, 4)
-                              for k in ("left_sweep_cycles", "svd_cycles", "svd_small_cycles",
+                              for k in ("left_sweep_cycles", "svd_cycles", "svd_small_cycles", "svd_qr_cycles",
                                         "right_sweep_rest_cycles", "expectation_cycles", "gauge_cycles")},
-              "per_shot_segment": {"svds_shared_memory": dprof["svd_count_shared"] / shot_segs,
-                                   "svds_large_bond": dprof["svd_count_large"] / shot_segs,
-                                   "gauge_sites": dprof["gauge_sites"] / shot_segs},
+              "per_shot_step": {"svds_shared_memory": dprof["svd_count_shared"] / shot_segs,
+                                "svds_large_bond": dprof["svd_count_large"] / shot_segs,
+                                "gauge_sites": dprof["gauge_sites"] / shot_segs,
+                                "jacobi_sweeps_per_large_svd": dprof["jacobi_sweeps_large"]
+                                / max(1.0, dprof["svd_count_large"])},
               "source": "stn_profile_counters: SM clock cycles of each CTA per phase over the timed steps"}
     if pg:
         t = torch.tensor([secs, host_s, kernel_s], dtype=torch.float64, device="cuda")
@@ -464,11 +473,13 @@ def main():
                 "vs_baseline": None, "dtype": "c64" if w.precision else "c128", "data": "synthetic",
                 "config": {"workload": w.name, "distance": w.distance, "rounds": w.rounds, "theta": w.theta,
                            "p": w.p, "chi_cap": w.chi_cap, "shots_per_batch_per_rank": B,
-                           "step": "one program segment (syndrome round or final readout) over the batch",
+                           "step": "one layer step over the batch: CNOT layer l of round r with its crosstalk "
+                                   "rotations (the round's H gates and ancilla measurements in its first and last "
+                                   "layer, the final readout in the last step); 4 x 5 = 20 steps = one batch",
                            "counted": counted,
                            "batch_vs_config": f"the configuration's 16,384 shots run as batches of {B} "
-                                              "resident shots (one per SM); a batch's segments are "
-                                              "one launch each",
+                                              "resident shots (one per SM, one CTA each); every layer step "
+                                              "of a batch is one launch",
                            "l2": "per-shot MPS state (GBs in all) larger than L2; no flush",
                            "parallelism": f"shots sharded over {ws} rank(s)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -54,6 +54,7 @@ typedef enum {
 enum { STN_PAIRS_ADJACENT_IDLE = 0, STN_PAIRS_ADJACENT_IDLE_DIAG_XX = 1 };
 enum { STN_PRECISION_C128 = 0, STN_PRECISION_C64 = 1 };
 enum { STN_BASIS_Z = 0, STN_BASIS_X = 1 };
+enum { STN_LAYERS_IDLE = 0xFF }; /* pair_layer_mask entry: use the idle rule */
 
 /* Simulation parameters: the problem statement of Sec. II-III (code
  * distance, rounds, CNOT schedule, crosstalk pairs and angles, Pauli noise
@@ -94,8 +95,9 @@ typedef struct {
   const int32_t *pairs;           /* [K][2] qubits of crosstalk pair k (Eq. 4) */
   const uint8_t *pair_pauli;      /* [K] 0: exp(-i theta Z Z), 1: X X; NULL = ZZ */
   const uint8_t *pair_layer_mask; /* [K] bit l: the rotation acts after CNOT
-                            layer l; NULL = after every layer in which no CNOT
-                            acts on exactly that pair (Sec. III B, Fig. 1) */
+                            layer l; STN_LAYERS_IDLE (or a NULL array) = after
+                            every layer in which no CNOT acts on exactly that
+                            pair (Sec. III B, Fig. 1) */
   int64_t arena_cap_bytes; /* 0: each resident shot's stack of doubled span
                             tensors and R factors is sized for the largest
                             span the cap allows; > 0: that stack is capped at
@@ -168,6 +170,18 @@ stn_status stn_apply_round(stn_ctx *ctx, int32_t round, const double *h_theta);
 
 /* Same, with the angles already in device memory (d_theta[K], doubles). */
 stn_status stn_apply_round_device(stn_ctx *ctx, int32_t round, const double *d_theta);
+
+/* The same program in finer launches: layer step s (0 .. 4 rounds - 1) is
+ * CNOT layer s % 4 of syndrome round s / 4 (Fig. 1) with the crosstalk
+ * rotations after it (Sec. III B); the first layer of a round also holds the
+ * round's opening H gates (round 0: the initial resets too), the last layer
+ * its closing H gates and ancilla measurements, and the last step the final
+ * data readout.  Running steps 0..4 rounds - 1 in order does exactly what
+ * running rounds 0..rounds does.  stn_num_steps returns 4 rounds.  One
+ * persistent kernel launch per step, angles d_theta[K] in device memory.
+ * Asynchronous.  Errors: STN_EINVAL for a bad step or no batch. */
+int32_t stn_num_steps(const stn_ctx *ctx);
+stn_status stn_apply_step_device(stn_ctx *ctx, int32_t step, const double *d_theta);
 
 /* Wait for the stream and report any device-side failure of the batch. */
 stn_status stn_sync(stn_ctx *ctx);

@@ -51,12 +51,11 @@ def config_from_workload(w):
         cfg.n_pairs = len(pairs)
         cfg.pairs = ab.ctypes.data
         cfg.pair_pauli = pauli.ctypes.data
-        if all(m is not None for _, _, _, m in pairs):
-            mask = np.ascontiguousarray([m for _, _, _, m in pairs], dtype=np.uint8)
+        if any(m is not None for _, _, _, m in pairs):  # None: the idle rule (STN_LAYERS_IDLE)
+            mask = np.ascontiguousarray([0xFF if m is None else int(m) & 0xF for _, _, _, m in pairs],
+                                        dtype=np.uint8)
             keep.append(mask)
             cfg.pair_layer_mask = mask.ctypes.data
-        elif any(m is not None for _, _, _, m in pairs):
-            raise ValueError("give a layer mask for every explicit pair or for none")
     cfg._keep = keep
     return cfg
 
@@ -133,6 +132,14 @@ class Simulator:
 
     def apply_round_device(self, r, d_theta_ptr):
         self._check(self.lib.stn_apply_round_device(self.ctx, int(r), ctypes.c_void_p(d_theta_ptr)))
+
+    @property
+    def n_steps(self):
+        """Layer steps of the program (4 per round, see stn_apply_step_device)."""
+        return self.lib.stn_num_steps(self.ctx)
+
+    def apply_step_device(self, step, d_theta_ptr):
+        self._check(self.lib.stn_apply_step_device(self.ctx, int(step), ctypes.c_void_p(d_theta_ptr)))
 
     def sync(self):
         self._check(self.lib.stn_sync(self.ctx))

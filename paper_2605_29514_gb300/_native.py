@@ -102,6 +102,8 @@ EXPORTS = [
     ("stn_begin_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64]),
     ("stn_apply_round", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     ("stn_apply_round_device", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    ("stn_num_steps", ctypes.c_int32, [ctypes.c_void_p]),
+    ("stn_apply_step_device", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     ("stn_sync", ctypes.c_int, [ctypes.c_void_p]),
     ("stn_read_records", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p]),

@@ -68,11 +68,11 @@ cudaError_t dalloc(stn_ctx *c, P **ptr, size_t bytes) {
   return e;
 }
 
-stn::EngineParams params(const stn_ctx *c, int seg, const double *d_theta) {
+stn::EngineParams params(const stn_ctx *c, int op_begin, int op_end, const double *d_theta) {
   stn::EngineParams p{};
   p.ops = c->d_ops;
-  p.op_begin = c->prog.seg_begin[seg];
-  p.op_end = c->prog.seg_begin[seg + 1];
+  p.op_begin = op_begin;
+  p.op_end = op_end;
   p.theta = d_theta;
   p.n = c->n;
   p.W = c->W;
@@ -160,7 +160,8 @@ std::string make_spec(const stn_config *cfg, stn::ProgramSpec &sp) {
       p.a = cfg->pairs[2 * k];
       p.b = cfg->pairs[2 * k + 1];
       p.pauli = cfg->pair_pauli ? cfg->pair_pauli[k] : 0;
-      p.layer_mask = cfg->pair_layer_mask ? (cfg->pair_layer_mask[k] & 0xF) : -1;
+      const int lm = cfg->pair_layer_mask ? cfg->pair_layer_mask[k] : STN_LAYERS_IDLE;
+      p.layer_mask = lm == STN_LAYERS_IDLE ? -1 : (lm & 0xF);
       sp.pairs.push_back(p);
     }
   }
@@ -390,22 +391,34 @@ stn_status stn_begin_batch(stn_ctx *c, int64_t shots, uint64_t shot_offset) {
   c->shot_offset = shot_offset;
   cudaError_t e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "stn_begin_batch");
-  stn::EngineParams p = params(c, 0, c->d_theta);
+  stn::EngineParams p = params(c, 0, 0, c->d_theta);
   e = stn::launch_init(c->cfg.precision, p, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
   return STN_OK;
 }
 
-stn_status stn_apply_round_device(stn_ctx *c, int32_t round, const double *d_theta) {
-  if (!c) return STN_EINVAL;
+static stn_status launch_ops(stn_ctx *c, int op_begin, int op_end, const double *d_theta) {
   if (c->shots < 1) return fail(c, STN_EINVAL, "no batch: call stn_begin_batch first");
-  if (round < 0 || round > c->cfg.rounds) return fail(c, STN_EINVAL, "round must be 0..rounds");
   if (!d_theta && c->K > 0) return fail(c, STN_EINVAL, "theta is NULL");
-  stn::EngineParams p = params(c, round, d_theta ? d_theta : c->d_theta);
+  stn::EngineParams p = params(c, op_begin, op_end, d_theta ? d_theta : c->d_theta);
   int grid = static_cast<int>(std::min<int64_t>(c->grid, c->shots));
   cudaError_t e = stn::launch_round(c->cfg.precision, p, grid, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "round kernel");
   return STN_OK;
+}
+
+stn_status stn_apply_round_device(stn_ctx *c, int32_t round, const double *d_theta) {
+  if (!c) return STN_EINVAL;
+  if (round < 0 || round > c->cfg.rounds) return fail(c, STN_EINVAL, "round must be 0..rounds");
+  return launch_ops(c, c->prog.seg_begin[round], c->prog.seg_begin[round + 1], d_theta);
+}
+
+int32_t stn_num_steps(const stn_ctx *c) { return c ? static_cast<int32_t>(c->prog.step_begin.size()) - 1 : -1; }
+
+stn_status stn_apply_step_device(stn_ctx *c, int32_t step, const double *d_theta) {
+  if (!c) return STN_EINVAL;
+  if (step < 0 || step >= stn_num_steps(c)) return fail(c, STN_EINVAL, "step must be 0..4 rounds - 1");
+  return launch_ops(c, c->prog.step_begin[step], c->prog.step_begin[step + 1], d_theta);
 }
 
 stn_status stn_apply_round(stn_ctx *c, int32_t round, const double *h_theta) {

@@ -150,6 +150,7 @@ std::string build_program(const ProgramSpec &spec, Program &P) {
   // Program.  Events in program order.
   int ev = 0, rec = 0;
   P.seg_begin.push_back(0);
+  P.step_begin.push_back(0);
   for (int q = 0; q < P.n; ++q) P.ops.push_back(make_op(OP_RESET_FLIP, q, 0, 0, ev++, 0));
   if (P.basis == 1) {  // X-memory: data qubits start in |+>
     for (int q : P.data) {
@@ -161,12 +162,16 @@ std::string build_program(const ProgramSpec &spec, Program &P) {
   for (int a : P.anc)
     if (P.kind[a] == 'X') xanc.push_back(a);
   for (int r = 0; r < rounds; ++r) {
-    if (r > 0) P.seg_begin.push_back(static_cast<int>(P.ops.size()));
+    if (r > 0) {
+      P.seg_begin.push_back(static_cast<int>(P.ops.size()));
+      P.step_begin.push_back(static_cast<int>(P.ops.size()));
+    }
     for (int a : xanc) {
       P.ops.push_back(make_op(OP_H, a, 0, 0, 0, 0));
       P.ops.push_back(make_op(OP_NOISE1, a, 0, 0, ev++, 0));
     }
     for (int l = 0; l < 4; ++l) {
+      if (l > 0) P.step_begin.push_back(static_cast<int>(P.ops.size()));
       for (size_t ai = 0; ai < P.anc.size(); ++ai) {
         int a = P.anc[ai], dq = P.slots[4 * ai + l];
         if (dq < 0) continue;
@@ -201,6 +206,7 @@ std::string build_program(const ProgramSpec &spec, Program &P) {
     ev += 2;
   }
   P.seg_begin.push_back(static_cast<int>(P.ops.size()));
+  P.step_begin.push_back(static_cast<int>(P.ops.size()));
   P.n_events = ev;
   P.n_meas = rec;
 

@@ -54,6 +54,12 @@ struct Program {
   std::vector<Pair> pairs;
   std::vector<Op> ops;
   std::vector<int> seg_begin;   // rounds + 2 entries: segment r = [seg_begin[r], seg_begin[r+1])
+  // 4 rounds + 1 entries: layer step s = [step_begin[s], step_begin[s+1]) is
+  // CNOT layer s % 4 of round s / 4 with its crosstalk rotations; the first
+  // layer of a round also holds the round's opening H gates (and, in round
+  // 0, the initial resets), the last one its closing H gates and ancilla
+  // measurements, and the very last step the final data readout
+  std::vector<int> step_begin;
   int n_events = 0, n_meas = 0;
   // Detectors of the Z-memory experiment: [n_det][kDetWidth] record indices
   // whose XOR is the detector bit (-1 pads); logical: record indices of the

@@ -1,0 +1,198 @@
+"""Host-side decoding of the memory experiment, off the timed path.
+
+The paper decodes the syndromes with minimum-weight matching under an error
+model built from the Pauli twirling approximation of the crosstalk (Sec. III C,
+Eq. 6): a rotation exp(-i theta P) is replaced by the Pauli P applied with
+probability sin^2 theta, and the circuit's Pauli noise (Eq. 2-3, Table I)
+enters with its own rates.  This module builds that error model from the
+library's compiled program (stn_compile_program, stn_compile_detectors) by
+Pauli-frame propagation through the Clifford part of the circuit, and decodes
+with a lookup table over all fault sets of up to two faults: each syndrome
+maps to the logical flip of larger total probability among the fault sets
+that produce it.
+
+Everything here is integer bookkeeping on the host; the simulation itself
+never calls it.
+"""
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import compile_detectors, compile_program
+
+OP_RESET_FLIP, OP_H, OP_NOISE1, OP_CNOT, OP_NOISE2, OP_ROT, OP_MEAS = 1, 2, 3, 4, 5, 6, 7
+
+
+@dataclass
+class FaultModel:
+    """Independent fault locations of the circuit: fault f applies its Pauli
+    with probability prob[f] and flips the detectors det[f] (bool, [F, n_det])
+    and the logical observable obs[f]."""
+    prob: np.ndarray
+    det: np.ndarray
+    obs: np.ndarray
+    kind: list  # per fault: ("rot", op index, pair) or ("noise", op index, pauli label)
+
+
+def _propagate(ops, n, n_meas, inject):
+    """Record flips [F, n_meas] of F Pauli faults.  inject[i] lists the
+    (fault row, x bits, z bits) applied right after op i (x, z: dicts qubit ->
+    bit).  Clifford gates move the frame (H swaps X and Z; CNOT copies X from
+    control to target and Z from target to control); a Z measurement records
+    the frame's X on its qubit, and a reset clears the qubit's frame."""
+    F = sum(len(v) for v in inject.values())
+    x = np.zeros((F, n), dtype=bool)
+    z = np.zeros((F, n), dtype=bool)
+    flips = np.zeros((F, n_meas), dtype=bool)
+    for i, (kind, a, b, pauli, _, idx) in enumerate(ops):
+        if kind == OP_H:
+            x[:, a], z[:, a] = z[:, a].copy(), x[:, a].copy()
+        elif kind == OP_CNOT:
+            x[:, b] ^= x[:, a]
+            z[:, a] ^= z[:, b]
+        elif kind == OP_MEAS:
+            flips[:, idx] = x[:, a]
+            if pauli == 1:  # measured ancilla reset to |0>: its frame is cleared
+                x[:, a] = False
+                z[:, a] = False
+        for row, xs, zs in inject.get(i, ()):
+            for q, v in xs.items():
+                x[row, q] ^= v
+            for q, v in zs.items():
+                z[row, q] ^= v
+    return flips
+
+
+def _apply_tables(flips, det_table, logical):
+    ext = np.concatenate([flips, np.zeros((flips.shape[0], 1), dtype=bool)], axis=1)  # index -1: zero
+    det = np.bitwise_xor.reduce(ext[:, det_table], axis=2)
+    obs = np.bitwise_xor.reduce(flips[:, logical], axis=1) if len(logical) else np.zeros(len(flips), bool)
+    return det, obs
+
+
+def build_fault_model(workload, theta, include_pauli_noise=True):
+    """Fault model of `workload` with per-pair angles `theta` (radians): one
+    PTA fault per crosstalk rotation (its pair's Pauli with probability
+    sin^2 theta, Eq. 6), and, when the workload has Pauli noise and
+    include_pauli_noise, every single-qubit Pauli after H (p1/3 each), every
+    two-qubit Pauli after CNOT (p2/15 each), an X after each reset (pR) and a
+    flipped record after each measurement (pM), as in Table I."""
+    counts, ops, pairs = compile_program(workload)
+    n, n_meas = int(counts[0]), int(counts[2])
+    det_table, logical = compile_detectors(workload)
+    theta = np.asarray(theta, dtype=np.float64)
+    p = workload.p
+    p1, p2 = p * workload.p1_scale, p * workload.p2_scale
+    pR, pM = p * workload.pR_scale, p * workload.pM_scale
+    inject, prob, kinds = {}, [], []
+    meas_flip = []  # (fault row, record index)
+
+    def add(i, xs, zs, pr, kind):
+        inject.setdefault(i, []).append((len(prob), xs, zs))
+        prob.append(pr)
+        kinds.append(kind)
+
+    letters = {"X": (1, 0), "Y": (1, 1), "Z": (0, 1)}
+    for i, (kind, a, b, pauli, _, idx) in enumerate(ops):
+        if kind == OP_ROT:
+            q = float(np.sin(theta[idx]) ** 2)
+            if q > 0:
+                bit = {a: True, b: True}
+                add(i, bit if pauli == 1 else {}, {} if pauli == 1 else bit, q, ("rot", i, int(idx)))
+        elif not include_pauli_noise or p == 0:
+            continue
+        elif kind == OP_NOISE1 and p1 > 0:
+            for lab, (xb, zb) in letters.items():
+                add(i, {a: bool(xb)}, {a: bool(zb)}, p1 / 3, ("noise", i, lab))
+        elif kind == OP_NOISE2 and p2 > 0:
+            for k in range(1, 16):
+                lc, lt = "IXYZ"[k // 4], "IXYZ"[k % 4]
+                xs, zs = {}, {}
+                for q, lab in ((a, lc), (b, lt)):
+                    if lab != "I":
+                        xs[q], zs[q] = bool(letters[lab][0]), bool(letters[lab][1])
+                add(i, xs, zs, p2 / 15, ("noise", i, lc + lt))
+        elif kind == OP_RESET_FLIP and pR > 0:
+            add(i, {a: True}, {}, pR, ("noise", i, "reset"))
+        elif kind == OP_MEAS:
+            if pM > 0:
+                meas_flip.append((len(prob), int(idx)))
+                add(i, {}, {}, pM, ("noise", i, "record"))
+            if pauli == 1 and pR > 0:
+                add(i, {a: True}, {}, pR, ("noise", i, "reset"))
+    flips = _propagate(ops, n, n_meas, inject)
+    for row, rec in meas_flip:
+        flips[row, rec] ^= True
+    det, obs = _apply_tables(flips, det_table, logical)
+    return FaultModel(np.array(prob), det, obs, kinds)
+
+
+def _key(bits):
+    return np.packbits(bits, bitorder="little").tobytes()
+
+
+class LookupDecoder:
+    """Syndrome -> predicted logical flip, from all fault sets of at most two
+    faults of a FaultModel (the lookup-table decoder of the d = 3 workload).
+    A syndrome outside the table is predicted as no flip and counted."""
+
+    def __init__(self, model, max_faults=2):
+        acc = {}
+
+        def put(key, flip, w):
+            e = acc.setdefault(key, [0.0, 0.0])
+            e[int(flip)] += w
+
+        q = model.prob
+        q0 = float(np.prod(1.0 - q))
+        put(_key(np.zeros(model.det.shape[1], dtype=bool)), False, q0)
+        odds = q / (1.0 - q)
+        for f in range(len(q)):
+            put(_key(model.det[f]), model.obs[f], q0 * odds[f])
+        if max_faults >= 2:
+            F = len(q)
+            for f in range(F):
+                g = np.arange(f + 1, F)
+                if len(g) == 0:
+                    continue
+                dets = model.det[f] ^ model.det[g]
+                obs = model.obs[f] ^ model.obs[g]
+                w = q0 * odds[f] * odds[g]
+                keys = np.packbits(dets, axis=1, bitorder="little")
+                for k, o, ww in zip(keys, obs, w):
+                    put(k.tobytes(), o, float(ww))
+        self.table = {k: int(v[1] > v[0]) for k, v in acc.items()}
+        self.n_det = model.det.shape[1]
+        self.unseen = 0
+
+    def predict(self, det_bits):
+        """Predicted logical flips of detector rows [shots, n_det] (0/1)."""
+        det_bits = np.asarray(det_bits, dtype=bool)
+        out = np.zeros(len(det_bits), dtype=np.uint8)
+        for s, row in enumerate(det_bits):
+            v = self.table.get(_key(row))
+            if v is None:
+                self.unseen += 1
+                v = 0
+            out[s] = v
+        return out
+
+
+def logical_error_rate(decoder, det_bits, observed):
+    """Fraction of shots whose predicted flip differs from the observed
+    logical parity, and that count."""
+    pred = decoder.predict(det_bits)
+    fails = int(np.sum(pred != np.asarray(observed, dtype=np.uint8)))
+    return fails / max(1, len(pred)), fails
+
+
+def wilson_interval(k, n, z=1.959963984540054):
+    """95% Wilson score interval of a binomial proportion k / n."""
+    if n == 0:
+        return 0.0, 1.0
+    ph = k / n
+    den = 1 + z * z / n
+    c = (ph + z * z / (2 * n)) / den
+    h = z * np.sqrt(ph * (1 - ph) / n + z * z / (4 * n * n)) / den
+    return max(0.0, c - h), min(1.0, c + h)

@@ -69,8 +69,9 @@ class Dense:
         return b, pb
 
 
-def run_dense(w, program, theta, shot):
-    """Records and realised Born probabilities of one shot."""
+def run_dense(w, program, theta, shot, max_ops=None, return_state=False):
+    """Records and realised Born probabilities of one shot (and the dense
+    state after the first max_ops ops when return_state)."""
     n = program.layout.n
     st = Dense(n)
     p = w.p
@@ -81,7 +82,9 @@ def run_dense(w, program, theta, shot):
     def u(ev):
         return uniform(w.seed, shot, ev)
 
-    for op in program.ops:
+    for i, op in enumerate(program.ops):
+        if max_ops is not None and i >= max_ops:
+            break
         kind = op[0]
         if kind == "RN":
             if u(op[2]) < pR:
@@ -116,4 +119,6 @@ def run_dense(w, program, theta, shot):
                     st.apply1(q, _PAULI["X"])
                 if u(evr) < pR:
                     st.apply1(q, _PAULI["X"])
+    if return_state:
+        return record, born, st
     return record, born

@@ -1,0 +1,82 @@
+"""CPU pins of the host decoder (paper_2605_29514_gb300.decoder): the PTA
+fault signatures it derives by Pauli-frame propagation through the compiled
+program equal what the oracle's full simulation records when that Pauli is
+actually applied (a rotation by theta = pi/2 is exp(-i pi/2 P) = -i P, a
+Pauli); the lookup table decodes the fault-free syndrome as no flip and most
+single faults correctly at d = 3; the Wilson interval has its textbook
+values."""
+
+import math
+
+import numpy as np
+import pytest
+
+import paper_2605_29514_gb300 as stn
+from paper_2605_29514_gb300.decoder import LookupDecoder, build_fault_model, wilson_interval
+from oracle.circuit import detectors, logical_z
+from oracle.shot import make_program, run_shot
+from workloads import D3_EXACT, theta_table
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    stn.build()
+
+
+@pytest.mark.parametrize("rule,pair", [("adjacent_idle", 0), ("adjacent_idle", 7), ("adjacent_idle", 23),
+                                       ("adjacent_idle+diag_xx", 30)])
+def test_fault_signatures_match_oracle_with_applied_paulis(rule, pair):
+    """theta = pi/2 on one pair and 0 elsewhere applies that pair's Pauli at
+    each of its occurrences: the oracle's detectors and logical parity equal
+    the XOR of the model's signatures of those occurrences."""
+    w = D3_EXACT.with_(rounds=2, p=0.0, pair_rule=rule)
+    prog = make_program(w)
+    theta = np.zeros(len(prog.pairs))
+    theta[pair] = math.pi / 2
+    model = build_fault_model(w, theta)
+    rows = [f for f, k in enumerate(model.kind) if k[0] == "rot" and k[2] == pair]
+    assert len(rows) == 2 * bin(prog.pairs[pair].layer_mask).count("1")
+    want_det = np.bitwise_xor.reduce(model.det[rows], axis=0)
+    want_obs = int(np.bitwise_xor.reduce(model.obs[rows]))
+    for shot in range(3):
+        r = run_shot(w, shot, theta, prog)
+        assert detectors(prog, r.record) == list(want_det.astype(int))
+        assert logical_z(prog, r.record) == want_obs
+
+
+def test_record_flip_faults_flip_their_detectors():
+    """A flipped record (Table I, pM) flips exactly the detectors that read
+    that record, and the logical parity when the record is one of its
+    readouts."""
+    w = D3_EXACT.with_(rounds=2, p=0.01, theta=0.0)
+    model = build_fault_model(w, np.zeros(24))
+    det_table, logical = stn.compile_detectors(w)
+    recs = [k for k in model.kind if k[0] == "noise" and k[2] == "record"]
+    assert len(recs) == w.n_meas
+    for f, k in enumerate(model.kind):
+        if k[0] == "noise" and k[2] == "record":
+            ops = stn.compile_program(w)[1]
+            rec = int(ops[k[1], 5])
+            expect = np.any(det_table == rec, axis=1)
+            assert np.array_equal(model.det[f], expect)
+            assert bool(model.obs[f]) == bool(rec in set(logical.tolist()))
+
+
+def test_lookup_decoder_on_single_faults():
+    w = D3_EXACT
+    prog = make_program(w)
+    theta = theta_table(w, len(prog.pairs))
+    model = build_fault_model(w, theta)
+    dec = LookupDecoder(model)
+    assert dec.predict(np.zeros((1, model.det.shape[1]), dtype=np.uint8))[0] == 0
+    pred = dec.predict(model.det.astype(np.uint8))
+    ok = np.mean(pred == model.obs.astype(np.uint8))
+    assert ok > 0.9, ok
+    assert dec.unseen == 0
+
+
+def test_wilson_interval():
+    lo, hi = wilson_interval(0, 100)
+    assert abs(lo) < 1e-12 and abs(hi - 0.03699) < 1e-4
+    lo, hi = wilson_interval(50, 100)
+    assert abs(lo - 0.40383) < 1e-4 and abs(hi - 0.59617) < 1e-4

@@ -89,3 +89,20 @@ def test_non_finite_theta_rejected(bad):
     out = sim.sample_shots(2, 0, theta)
     ref = run_shot(w, 1, theta)
     assert list(out["bits"][1]) == ref.record
+
+
+def test_layer_steps_equal_rounds():
+    """Running the 4 x rounds layer steps in order gives the same records,
+    Born probabilities and statistics as running the round segments."""
+    w = D3_EXACT.with_(p=0.02)
+    shots = 6
+    _, base, theta = gpu_run(w, shots)
+    sim = stn.Simulator(w, max_shots=shots)
+    assert sim.n_steps == 4 * w.rounds
+    d_theta = torch.tensor(theta, dtype=torch.float64, device="cuda")
+    sim.begin_batch(shots, 0)
+    for s in range(sim.n_steps):
+        sim.apply_step_device(s, d_theta.data_ptr())
+    out = sim.read_records()
+    for key in ("records", "born", "max_chi", "logp", "discarded"):
+        assert np.array_equal(out[key], base[key]), key
