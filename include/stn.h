@@ -254,14 +254,54 @@ stn_status stn_read_bonds(stn_ctx *ctx, int64_t shot, int32_t *h_bonds);
  * Errors: STN_EINVAL for a bad shot or site. */
 stn_status stn_read_site(stn_ctx *ctx, int64_t shot, int32_t k, void *h_site);
 
+/* Expectation of the memory's logical operator on every shot of the current
+ * batch (synchronises): Z_L (Z on the top data row) for a Z-memory, X_L (X
+ * on the left data column) for an X-memory, evaluated on the present state
+ * C|MPS> (Eq. 7) by pushing it through the frame and contracting the MPS over
+ * its support.  Called after the syndrome rounds and before the final
+ * readout, it gives the logical angle behind the P_L estimator of Sec. II,
+ * Eq. 1: with the decoder's correction c, sin^2(theta/2) = (1 - (-1)^c <L>)/2.
+ * h_out[shots] (host, caller-owned); NaN for a shot stopped by an error.
+ * Moves each shot's orthogonality centre by exact gauge steps only.
+ * Errors: STN_EINVAL without a batch. */
+stn_status stn_logical_expectation(stn_ctx *ctx, double *h_out);
+
+/* Squared Schmidt coefficients of one shot's MPS across the cut between sites
+ * `cut` and `cut` + 1 (Sec. IV B, Fig. 2 shows them at the centre cut),
+ * largest first, into h_sig2 (host, caller-owned, room for chi_cap values);
+ * *h_count receives their number.  The shot's orthogonality centre is moved
+ * to site `cut` by exact gauge steps (synchronises).  Errors: STN_EINVAL for a
+ * bad shot or cut. */
+stn_status stn_schmidt_values(stn_ctx *ctx, int64_t shot, int32_t cut, double *h_sig2, int32_t *h_count);
+
 /* Whole job: begin_batch, every segment with h_theta, read_records. */
 stn_status stn_sample_shots(stn_ctx *ctx, int64_t shots, uint64_t shot_offset,
                             const double *h_theta, uint8_t *h_records, double *h_born,
                             stn_shot_stats *h_stats);
 
-/* Gradient of log P(fixed record) with respect to the K crosstalk angles.
- * Not implemented: returns STN_ENOTIMPL. */
-stn_status stn_logprob_grad(stn_ctx *ctx, const uint8_t *h_records, int64_t n_rec,
+/* Log-likelihood of fixed measurement records and its gradient with respect
+ * to the K per-pair crosstalk angles (the rotation of Eq. 4 in the stabilizer
+ * tensor network of Eq. 7), by the adjoint method.  Record r (h_records
+ * [n_rec][ceil(n_meas/8)], packed as in stn_read_records) belongs to global
+ * shot shot_offset + r, whose Pauli-noise and record-flip events stay the
+ * shot's own Philox draws: P(record) is the probability of the record with
+ * that noise realisation held fixed, so each measurement's outcome is forced
+ * to the record bit XOR its flip event.  Forward pass: the forced shot on
+ * the GPU, keeping the state after every rotation and each op's conjugated
+ * Pauli; h_logp[r] = sum of the log Born probabilities of the forced
+ * outcomes (-inf with STN_ENUMERIC for a record of probability zero).
+ * Backward pass: from the final state mu, op by op to the first, rotation j
+ * of pair k adds 2 Re <mu|(-i P'_j)|phi_j> / <mu|phi_j> to h_grad[k] and then
+ * mu <- exp(+i theta P'_j) mu; a case-A measurement projector is applied
+ * again, a case-B measurement applies U |v><0|_j; each application is
+ * followed by the same truncating sweep (Sec. IV B), so the result is the
+ * gradient of the truncated simulation, exact when nothing is truncated.
+ * h_grad[K] is summed over the n_rec records (host, caller-owned).  Uses the
+ * context's shot slots (n_rec <= max_shots): the current batch is replaced.
+ * Allocates device memory for one state per rotation and record for the
+ * duration of the call (STN_ENOMEM when it does not fit).  Errors:
+ * STN_EINVAL, STN_ENOMEM, STN_ENUMERIC, STN_ECUDA. */
+stn_status stn_logprob_grad(stn_ctx *ctx, uint64_t shot_offset, int64_t n_rec, const uint8_t *h_records,
                             const double *h_theta, double *h_logp, double *h_grad);
 
 /* Philox4x32-10 uniforms u = ((w0<<21) ^ (w1>>11)) * 2^-53 for shots

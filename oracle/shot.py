@@ -104,6 +104,12 @@ class ShotSim:
         self.near = 0
         self.want_trace = trace
         self.trace = []
+        # forced outcomes (the adjoint's forward pass): record bits to
+        # reproduce, each outcome being the record bit XOR its record flip
+        self.forced = None
+        # with a list here, rotations and measurements append what the
+        # adjoint's backward pass needs (see oracle.adjoint)
+        self.tape = None
 
     def u(self, ev):
         return uniform(self.w.seed, self.shot, ev)
@@ -165,6 +171,8 @@ class ShotSim:
         w1 = -1j * math.sin(th) * (1j ** pp.m)
         self.mps.apply_two_branch(lo, hi, {}, ops1, math.cos(th), w1)
         self._compress(a, b, "rot")
+        if self.tape is not None:
+            self.tape.append(("rot", k, pp, lo, hi, self.mps.copy()))
 
     def measure(self, q, ev_b, ev_f, rec, reset, ev_r):
         zq = Pauli.single(self.n, q, "Z")
@@ -176,6 +184,8 @@ class ShotSim:
         p0 = min(1.0, max(0.0, 0.5 * (1.0 + e)))
         u = self.u(ev_b)
         b = 0 if u < p0 else 1
+        if self.forced is not None:
+            b = self.forced[rec] ^ (1 if self.u(ev_f) < self.pM else 0)
         if abs(u - p0) < NEAR_THRESHOLD:
             self.near += 1
         pb = p0 if b == 0 else 1.0 - p0
@@ -186,6 +196,8 @@ class ShotSim:
             w1 = (1 if b == 0 else -1) * (1j ** pp.m) * 0.5
             self.mps.apply_two_branch(lo, hi, {}, ops, 0.5, w1)
             self._compress(sa, sb, "measA")
+            if self.tape is not None:
+                self.tape.append(("measA", ops, lo, hi, w1))
         else:
             j = int(np.flatnonzero(pp.x)[0])
             letters = pp.letters()
@@ -201,6 +213,8 @@ class ShotSim:
             v = EIGVEC[key]
             self.mps.apply_site(j, np.outer(np.array([1, 0], dtype=complex), v.conj()))
             self._compress(sa, sb, "measB")
+            if self.tape is not None:
+                self.tape.append(("measB", ops1, lo, hi, j, v))
             for s in supp:
                 s = int(s)
                 if s != j:

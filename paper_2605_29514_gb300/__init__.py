@@ -184,6 +184,21 @@ class Simulator:
         self._check(self.lib.stn_profile_counters(self.ctx, ctypes.cast(buf, ctypes.c_void_p)))
         return dict(zip(self.PROFILE_KEYS, list(buf)))
 
+    def logical_expectation(self):
+        """<L> of the memory's logical operator on every shot of the batch
+        (stn_logical_expectation); call after the syndrome rounds."""
+        out = np.zeros(self.shots, dtype=np.float64)
+        self._check(self.lib.stn_logical_expectation(self.ctx, _ptr(out)))
+        return out
+
+    def schmidt_values(self, shot, cut):
+        """Squared Schmidt coefficients across the cut after site `cut`
+        (stn_schmidt_values), largest first."""
+        out = np.zeros(max(512, self.cfg.chi_cap), dtype=np.float64)
+        cnt = ctypes.c_int32()
+        self._check(self.lib.stn_schmidt_values(self.ctx, int(shot), int(cut), _ptr(out), ctypes.byref(cnt)))
+        return out[: cnt.value]
+
     def read_records_into(self, h_records_ptr):
         """Packed records of the batch into caller-owned host memory
         ([shots][rec_bytes] bytes, e.g. pinned)."""
@@ -223,13 +238,16 @@ class Simulator:
             self.apply_round(r, theta)
         return self.read_records(born=born, stats=stats)
 
-    def logprob_grad(self, records, theta):
+    def logprob_grad(self, records, theta, shot_offset=0):
+        """(log P[r], d sum_r log P[r] / d theta[K]) of packed records
+        [n_rec][rec_bytes] of global shots shot_offset.. (stn_logprob_grad)."""
         rec = np.ascontiguousarray(records, dtype=np.uint8)
         theta = np.ascontiguousarray(theta, dtype=np.float64)
         logp = np.zeros(len(rec), dtype=np.float64)
         grad = np.zeros(self.n_pairs, dtype=np.float64)
-        self._check(self.lib.stn_logprob_grad(self.ctx, _ptr(rec), len(rec), _ptr(theta), _ptr(logp),
-                                              _ptr(grad)))
+        self._check(self.lib.stn_logprob_grad(self.ctx, int(shot_offset), len(rec), _ptr(rec), _ptr(theta),
+                                              _ptr(logp), _ptr(grad)))
+        self.shots = len(rec)
         return logp, grad
 
 

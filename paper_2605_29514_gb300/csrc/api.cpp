@@ -42,6 +42,9 @@ struct stn_ctx {
   int32_t *d_det_table = nullptr, *d_logical = nullptr;
   void *d_scratch = nullptr;
   int *d_err = nullptr;
+  double *d_diag = nullptr;     // diagnostics output: max(max_shots, 512) doubles
+  int *d_diag_count = nullptr;
+  int32_t *d_diag_q = nullptr;  // n qubit indices
   std::string last_error;
   std::vector<void *> allocs;
 };
@@ -177,6 +180,27 @@ std::string compile(const stn_config *cfg, stn::Program &prog) {
 
 }  // namespace
 
+namespace {
+// Device buffers of one adjoint call, freed when it returns.
+struct AdjointBuffers {
+  std::vector<void *> ptrs;
+  ~AdjointBuffers() {
+    for (void *p : ptrs) cudaFree(p);
+  }
+  template <typename P>
+  bool get(P **out, size_t bytes) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    ptrs.push_back(p);
+    *out = static_cast<P *>(p);
+    return true;
+  }
+};
+}  // namespace
+
 extern "C" {
 
 int32_t stn_layout(int32_t distance, int32_t *h_xy, char *h_kind) {
@@ -287,6 +311,9 @@ stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_strea
   A(dalloc(c, &c->d_logical, sizeof(int32_t) * c->prog.logical.size()));
   A(dalloc(c, &c->d_scratch, c->elem * static_cast<size_t>(c->grid) * c->plan.total));
   A(dalloc(c, &c->d_err, sizeof(int)));
+  A(dalloc(c, &c->d_diag, sizeof(double) * std::max<int64_t>(S, 512)));
+  A(dalloc(c, &c->d_diag_count, sizeof(int)));
+  A(dalloc(c, &c->d_diag_q, sizeof(int32_t) * n));
   if (!ok) {
     stn_destroy(c);
     cudaGetLastError();
@@ -563,6 +590,51 @@ stn_status stn_read_site(stn_ctx *c, int64_t shot, int32_t k, void *h_site) {
   return STN_OK;
 }
 
+static cudaError_t launch_diag(stn_ctx *c, int what, int target, int cut, int nl, int letter, int grid) {
+  stn::EngineParams p = params(c, 0, 0, c->d_theta);
+  return c->cfg.precision == STN_PRECISION_C128
+             ? stn::launch_diag_f64(p, what, target, cut, c->d_diag_q, nl, letter, c->d_diag, c->d_diag_count,
+                                    grid, c->stream)
+             : stn::launch_diag_f32(p, what, target, cut, c->d_diag_q, nl, letter, c->d_diag, c->d_diag_count,
+                                    grid, c->stream);
+}
+
+stn_status stn_logical_expectation(stn_ctx *c, double *h_out) {
+  if (!c || !h_out) return fail(c, STN_EINVAL, "bad argument");
+  if (c->shots < 1) return fail(c, STN_EINVAL, "no batch");
+  std::vector<int32_t> lq;
+  const bool xmem = c->prog.basis == STN_BASIS_X;
+  for (int q : c->prog.data)
+    if ((!xmem && c->prog.xy[2 * q + 1] == 1) || (xmem && c->prog.xy[2 * q] == 1)) lq.push_back(q);
+  cudaError_t e = cudaMemcpyAsync(c->d_diag_q, lq.data(), sizeof(int32_t) * lq.size(), cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e == cudaSuccess)
+    e = launch_diag(c, 0, 0, 0, static_cast<int>(lq.size()), xmem ? 1 : 3,
+                    static_cast<int>(std::min<int64_t>(c->grid, c->shots)));
+  if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics kernel");
+  stn_status st = stn_sync(c);
+  if (st != STN_OK) return st;
+  e = cudaMemcpy(h_out, c->d_diag, sizeof(double) * c->shots, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stn_logical_expectation");
+  return STN_OK;
+}
+
+stn_status stn_schmidt_values(stn_ctx *c, int64_t shot, int32_t cut, double *h_sig2, int32_t *h_count) {
+  if (!c || !h_sig2 || !h_count || shot < 0 || shot >= c->shots || cut < 0 || cut > c->n - 2)
+    return fail(c, STN_EINVAL, "bad argument");
+  cudaError_t e = launch_diag(c, 1, static_cast<int>(shot), cut, 0, 0, 1);
+  if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics kernel");
+  stn_status st = stn_sync(c);
+  if (st != STN_OK) return st;
+  int cnt = 0;
+  e = cudaMemcpy(&cnt, c->d_diag_count, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && cnt > 0)
+    e = cudaMemcpy(h_sig2, c->d_diag, sizeof(double) * cnt, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stn_schmidt_values");
+  *h_count = cnt;
+  return STN_OK;
+}
+
 stn_status stn_sample_shots(stn_ctx *c, int64_t shots, uint64_t shot_offset, const double *h_theta,
                             uint8_t *h_records, double *h_born, stn_shot_stats *h_stats) {
   stn_status st = stn_begin_batch(c, shots, shot_offset);
@@ -571,9 +643,74 @@ stn_status stn_sample_shots(stn_ctx *c, int64_t shots, uint64_t shot_offset, con
   return stn_read_records(c, h_records, h_born, h_stats);
 }
 
-stn_status stn_logprob_grad(stn_ctx *c, const uint8_t *, int64_t, const double *, double *,
-                            double *) {
-  return fail(c, STN_ENOTIMPL, "stn_logprob_grad is not implemented");
+
+stn_status stn_logprob_grad(stn_ctx *c, uint64_t shot_offset, int64_t n_rec, const uint8_t *h_records,
+                            const double *h_theta, double *h_logp, double *h_grad) {
+  if (!c) return STN_EINVAL;
+  if (n_rec < 1 || n_rec > c->max_shots || !h_records || !h_logp || !h_grad || (!h_theta && c->K > 0))
+    return fail(c, STN_EINVAL, "stn_logprob_grad: bad argument");
+  for (int k = 0; k < c->K; ++k)
+    if (!std::isfinite(h_theta[k])) return fail(c, STN_EINVAL, "theta must be finite");
+  const int n_ops = static_cast<int>(c->prog.ops.size());
+  std::vector<int32_t> rot_ord(n_ops, -1);
+  int n_rot = 0;
+  for (int i = 0; i < n_ops; ++i)
+    if (c->prog.ops[i].kind == stn::OP_ROT) rot_ord[i] = n_rot++;
+  const size_t phi_bytes = c->elem * static_cast<size_t>(n_rec) * std::max(1, n_rot) * c->slab_elems;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "memory info");
+  if (phi_bytes > free_b / 10 * 8)
+    return fail(c, STN_ENOMEM, "stn_logprob_grad: the states after every rotation do not fit device memory");
+  AdjointBuffers buf;
+  uint8_t *d_forced = nullptr;
+  uint64_t *d_px = nullptr, *d_pz = nullptr;
+  int32_t *d_info = nullptr, *d_rot = nullptr;
+  void *d_phi = nullptr;
+  int *d_phi_chi = nullptr;
+  double *d_grad = nullptr;
+  const size_t tape = static_cast<size_t>(n_rec) * n_ops;
+  bool ok = buf.get(&d_forced, static_cast<size_t>(n_rec) * c->rec_bytes) &&
+            buf.get(&d_px, sizeof(uint64_t) * tape * c->W) && buf.get(&d_pz, sizeof(uint64_t) * tape * c->W) &&
+            buf.get(&d_info, sizeof(int32_t) * tape * stn::kTapeInts) &&
+            buf.get(&d_rot, sizeof(int32_t) * n_ops) && buf.get(&d_phi, phi_bytes) &&
+            buf.get(&d_phi_chi, sizeof(int) * static_cast<size_t>(n_rec) * std::max(1, n_rot) * (c->n + 1)) &&
+            buf.get(&d_grad, sizeof(double) * std::max(1, c->K));
+  if (!ok) return fail(c, STN_ENOMEM, "stn_logprob_grad: device allocation failed");
+  stn_status st = stn_begin_batch(c, n_rec, shot_offset);
+  if (st != STN_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(d_forced, h_records, static_cast<size_t>(n_rec) * c->rec_bytes,
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_rot, rot_ord.data(), sizeof(int32_t) * n_ops, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && c->K > 0)
+    e = cudaMemcpyAsync(c->d_theta, h_theta, sizeof(double) * c->K, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_grad, 0, sizeof(double) * std::max(1, c->K), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stn_logprob_grad copies");
+  stn::EngineParams p = params(c, 0, n_ops, c->d_theta);
+  p.forced = d_forced;
+  p.tape_px = d_px;
+  p.tape_pz = d_pz;
+  p.tape_info = d_info;
+  p.phi_store = d_phi;
+  p.phi_chi = d_phi_chi;
+  p.rot_ord = d_rot;
+  p.n_ops_total = n_ops;
+  p.n_rot = n_rot;
+  const int grid = static_cast<int>(std::min<int64_t>(c->grid, n_rec));
+  e = stn::launch_round(c->cfg.precision, p, grid, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint forward");
+  st = stn_sync(c);
+  if (st != STN_OK) return st;
+  e = cudaMemcpy(h_logp, c->d_logp, sizeof(double) * n_rec, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stn_logprob_grad logp");
+  e = c->cfg.precision == STN_PRECISION_C128 ? stn::launch_adjoint_f64(p, d_grad, grid, c->stream)
+                                             : stn::launch_adjoint_f32(p, d_grad, grid, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint backward");
+  st = stn_sync(c);
+  if (st != STN_OK) return st;
+  e = cudaMemcpy(h_grad, d_grad, sizeof(double) * c->K, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stn_logprob_grad grad");
+  return STN_OK;
 }
 
 stn_status stn_dense_qr_q(int32_t precision, int32_t m, int32_t n, void *d_b, void *d_q, void *d_work,

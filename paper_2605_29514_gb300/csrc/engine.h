@@ -54,7 +54,24 @@ struct EngineParams {
   int work_c;               // largest bond of the plan (sizes the work area)
   int svd_elems;            // complex elements of the shared-memory SVD buffer
   int *err;                 // first error code seen on the device
+  // Adjoint of log P(record) (all null in an ordinary run).  forced: records
+  // to reproduce, [shot][rec_bytes]; a measurement's outcome is then its
+  // record bit XOR its record-flip event.  With tape_info set, rotations and
+  // measurements write what the backward pass needs: the conjugated Pauli
+  // (tape_px/pz [shot][op][W]), tape_info [shot][op][kTapeInts], and after
+  // each rotation the state (phi_* [shot][rotation ordinal]).
+  const uint8_t *forced;
+  uint64_t *tape_px, *tape_pz;
+  int32_t *tape_info;
+  void *phi_store;          // [shot][n_rot][slab_elems] complex of the precision
+  int *phi_chi;             // [shot][n_rot][n + 1]
+  const int32_t *rot_ord;   // [op] ordinal of a rotation among the shot's rotations, -1 otherwise
+  int n_ops_total, n_rot;
 };
+
+// tape_info entries of an op: [0] phase m of P' | case B << 2 | outcome << 3
+// | lidx << 4 | sign(P') < 0 << 6, [1] lo, [2] hi, [3] j
+constexpr int kTapeInts = 4;
 
 struct ScratchPlan {
   int64_t ap_elems, g_elems, work_elems, total;
@@ -77,6 +94,12 @@ cudaError_t launch_dense_check_f32(int what, int m, int n, void *A, void *V, voi
 cudaError_t launch_dense_check_f64(int what, int m, int n, void *A, void *V, void *sig2, int use_smem,
                                    cudaStream_t s);
 cudaError_t launch_round(int precision, const EngineParams &p, int grid, cudaStream_t s);
+cudaError_t launch_adjoint_f32(const EngineParams &p, double *grad, int grid, cudaStream_t s);
+cudaError_t launch_adjoint_f64(const EngineParams &p, double *grad, int grid, cudaStream_t s);
+cudaError_t launch_diag_f32(const EngineParams &p, int what, int target, int cut, const int32_t *lq, int nl,
+                            int letter, double *out, int *count, int grid, cudaStream_t s);
+cudaError_t launch_diag_f64(const EngineParams &p, int what, int target, int cut, const int32_t *lq, int nl,
+                            int letter, double *out, int *count, int grid, cudaStream_t s);
 cudaError_t launch_dense_check(int precision, int what, int m, int n, void *A, void *V, void *sig2,
                                int use_smem, cudaStream_t s);
 int svd_smem_elems(int precision);

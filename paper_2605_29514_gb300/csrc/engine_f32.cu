@@ -14,4 +14,13 @@ cudaError_t launch_dense_check_f32(int what, int m, int n, void *A, void *V, voi
   return launch_dense_check_t<float>(what, m, n, A, V, sig2, use_smem, s);
 }
 
+cudaError_t launch_diag_f32(const EngineParams &p, int what, int target, int cut, const int32_t *lq, int nl,
+                            int letter, double *out, int *count, int grid, cudaStream_t s) {
+  return launch_diag_t<float>(p, what, target, cut, lq, nl, letter, out, count, grid, s);
+}
+
+cudaError_t launch_adjoint_f32(const EngineParams &p, double *grad, int grid, cudaStream_t s) {
+  return launch_adjoint_t<float>(p, grad, grid, s);
+}
+
 }  // namespace stn

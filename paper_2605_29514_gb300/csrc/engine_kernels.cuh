@@ -1094,7 +1094,9 @@ static __device__ void sort_desc(int n, const T *lam, int *perm) {
 
 // ---------------------------------------------------------------------------
 // The MPO of one rotation or measurement.
-enum MpoKind { MPO_ROT = 0, MPO_PROJ_Z = 1, MPO_PROJ_B = 2 };
+// MPO_ADJ_B: the adjoint of a case-B measurement, U |v><0|_j (U the
+// controlled-Pauli product of the measurement, |v> its site-j eigenvector).
+enum MpoKind { MPO_ROT = 0, MPO_PROJ_Z = 1, MPO_PROJ_B = 2, MPO_ADJ_B = 3 };
 
 template <typename T>
 struct MpoSpec {
@@ -1114,7 +1116,9 @@ static __device__ void site_op(const MpoSpec<T> &sp, const uint64_t *ppx, const 
   if (br == 1) {
     if (sp.kind == MPO_PROJ_B && k == sp.j) {
       op[0] = zero; op[1] = cconj(sp.v1); op[2] = zero; op[3] = zero;
-    } else if (sp.kind == MPO_PROJ_B) {
+    } else if (sp.kind == MPO_ADJ_B && k == sp.j) {  // v1 |1><0|
+      op[0] = zero; op[1] = zero; op[2] = sp.v1; op[3] = zero;
+    } else if (sp.kind == MPO_PROJ_B || sp.kind == MPO_ADJ_B) {
       // Hermitian letter of P' at k (controlled-Pauli target)
       if (x && !z) { op[0] = zero; op[1] = one; op[2] = one; op[3] = zero; }
       else if (x && z) { op[0] = zero; op[1] = cmake<T>(0, -1); op[2] = cmake<T>(0, 1); op[3] = zero; }
@@ -1127,6 +1131,8 @@ static __device__ void site_op(const MpoSpec<T> &sp, const uint64_t *ppx, const 
     }
   } else if (sp.kind == MPO_PROJ_B && k == sp.j) {
     op[0] = cconj(sp.v0); op[3] = zero;
+  } else if (sp.kind == MPO_ADJ_B && k == sp.j) {  // v0 |0><0|
+    op[0] = sp.v0; op[3] = zero;
   }
   if (k == sp.lo) {
     cplx<T> w = br == 0 ? sp.w0 : sp.w1;
@@ -1989,6 +1995,18 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
               sp.w1 = w1;
             }
             if (lo > hi) S.misc[M_FAIL] = STN_ENUMERIC;  // identity Pauli cannot occur
+            if (P.tape_info) {
+              const int64_t t = shot * P.n_ops_total + oi;
+              for (int w = 0; w < W; ++w) {
+                P.tape_px[t * W + w] = S.ppx[w];
+                P.tape_pz[t * W + w] = S.ppz[w];
+              }
+              int32_t *ti = P.tape_info + t * kTapeInts;
+              ti[0] = m & 3;
+              ti[1] = lo;
+              ti[2] = hi;
+              ti[3] = j;
+            }
           }
           __syncthreads();
           if (S.misc[M_FAIL]) break;
@@ -2024,15 +2042,23 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
             if (tid() == 0) {
               double p0 = small == 0 ? ps : 1.0 - ps;
               double u = philox_uniform(P.seed, gshot, op.ev);
+              const int flip = philox_uniform(P.seed, gshot, op.ev + 1) < P.pM ? 1 : 0;
               int bit = u < p0 ? 0 : 1;
+              if (P.forced)  // adjoint forward pass: the outcome that reproduces the record
+                bit = ((P.forced[shot * P.rec_bytes + op.idx / 8] >> (op.idx % 8)) & 1) ^ flip;
               double pb = bit == 0 ? p0 : 1.0 - p0;
-              if (fabs(u - p0) < kNearThreshold) P.near[shot] += 1;
+              if (!P.forced && fabs(u - p0) < kNearThreshold) P.near[shot] += 1;
               P.born[shot * P.n_meas + op.idx] = pb;
               S.dmisc[D_LOGP] += log(pb);
-              int flip = philox_uniform(P.seed, gshot, op.ev + 1) < P.pM ? 1 : 0;
               if (bit ^ flip) P.records[shot * P.rec_bytes + op.idx / 8] |= static_cast<uint8_t>(1u << (op.idx % 8));
               S.misc[M_OUTCOME] = bit;
               if (bit != small) set_meas_spec<T>(S, bit);
+              if (P.tape_info) {
+                int32_t *ti = P.tape_info + (shot * P.n_ops_total + oi) * kTapeInts;
+                const int mb = S.misc[M_BIT];
+                ti[0] = (mb & 3) | (S.misc[M_CASEB] << 2) | (bit << 3) | (S.misc[M_LIDX] << 4) |
+                        (((mb >> 4) & 1) << 6);
+              }
             }
             __syncthreads();
             caseB = S.misc[M_CASEB];
@@ -2049,6 +2075,16 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
             __syncthreads();
             prof_mark(S.dmisc, PROF_LEFT, tq);
             mps_finish<T>(P, S, shot, X, a, b);
+            if (P.phi_store && P.rot_ord[oi] >= 0) {  // adjoint: keep the state after the rotation
+              const int64_t slot = shot * P.n_rot + P.rot_ord[oi];
+              cplx<T> *dst = reinterpret_cast<cplx<T> *>(P.phi_store) + slot * P.slab_elems;
+              for (int k = 0; k < n; ++k) {
+                const cplx<T> *src = site_ptr<T>(P, shot, k);
+                const int64_t cnt = 2ll * S.chi[k] * S.chi[k + 1];
+                for (int64_t e = tid(); e < cnt; e += kThreads) dst[P.site_off[k] + e] = src[e];
+              }
+              for (int e = tid(); e <= n; e += kThreads) P.phi_chi[slot * (n + 1) + e] = S.chi[e];
+            }
           }
           if (meas) {
             if (caseB) tableau_caseB(S.tx, S.tz, S.tm, n, W, S.ppx, S.ppz, S.misc[M_J], lidx);
@@ -2193,6 +2229,282 @@ cudaError_t launch_init_t(const EngineParams &p, cudaStream_t s) {
   int grid = p.shots < 4096 ? p.shots : 4096;
   if (grid < 1) return cudaSuccess;
   init_kernel<T><<<grid, 128, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics of the current batch, one CTA per shot slot (grid-strided).
+// what = DIAG_LOGICAL: out[shot] = <psi| L |psi> for L the product of
+//   `letter` (1 X, 3 Z) over the nl qubits lq (Sec. II, Eq. 1: the logical
+//   operator's expectation behind the P_L estimator).  L is pushed through
+//   the shot's frame, P' = C^dag L C = i^m X^x Z^z (the images of the
+//   commuting factors multiplied with the exact phase), the orthogonality
+//   centre is moved into P''s support, and <MPS| P' |MPS> is contracted over
+//   it.  A shot whose status is set gets NaN.
+// what = DIAG_SCHMIDT: for shot `target` only, the centre is moved to site
+//   `cut` and the squared singular values of that site as a
+//   (2 chi_cut) x chi_{cut+1} matrix, the squared Schmidt coefficients across
+//   the cut after site `cut` (Sec. IV B, Fig. 2), go to out[] largest first,
+//   their number to *count.
+// Both only move the orthogonality centre by exact gauge steps: the state,
+// and every later result of the batch, are unchanged (up to rounding).
+enum { DIAG_LOGICAL = 0, DIAG_SCHMIDT = 1 };
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1) diag_kernel(EngineParams P, int what, int target, int cut,
+                                                           const int32_t *lq, int nl, int letter, double *out,
+                                                           int *count) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const int n = P.n, W = P.W;
+  Smem<T> S = carve<T>(smem_raw, n, W, P.svd_elems);
+  Scratch<T> X = scratch_for<T>(P, P.work_c);
+  for (int64_t shot = blockIdx.x; shot < P.shots; shot += gridDim.x) {
+    if (what == DIAG_SCHMIDT && shot != target) continue;
+    for (int e = tid(); e < 2 * n * W; e += kThreads) {
+      S.tx[e] = P.tab_x[shot * 2 * n * W + e];
+      S.tz[e] = P.tab_z[shot * 2 * n * W + e];
+    }
+    for (int e = tid(); e < 2 * n; e += kThreads) S.tm[e] = P.tab_m[shot * 2 * n + e];
+    for (int e = tid(); e <= n; e += kThreads) S.chi[e] = P.chi[shot * (n + 1) + e];
+    if (tid() == 0) {
+      S.misc[M_CENTER] = P.center[shot];
+      S.misc[M_FAIL] = P.status[shot];
+    }
+    __syncthreads();
+    if (S.misc[M_FAIL]) {
+      if (tid() == 0) {
+        if (what == DIAG_LOGICAL) out[shot] = nan("");
+        else *count = 0;
+      }
+      __syncthreads();
+      continue;
+    }
+    if (what == DIAG_LOGICAL) {
+      if (tid() == 0) {
+        for (int w = 0; w < W; ++w) S.ppx[w] = S.ppz[w] = 0;
+        int m = 0;
+        for (int i = 0; i < nl; ++i) {
+          const int r = letter == 3 ? n + lq[i] : lq[i];
+          int sw = 0;
+          for (int w = 0; w < W; ++w) {
+            sw += popc64(S.ppz[w] & S.tx[r * W + w]);
+            S.ppx[w] ^= S.tx[r * W + w];
+            S.ppz[w] ^= S.tz[r * W + w];
+          }
+          m += S.tm[r] + 2 * sw;
+        }
+        int lo = n, hi = -1;
+        for (int q = 0; q < n; ++q)
+          if (((S.ppx[q >> 6] | S.ppz[q >> 6]) >> (q & 63)) & 1) { lo = min(lo, q); hi = max(hi, q); }
+        S.misc[M_LO] = lo;
+        S.misc[M_HI] = hi;
+        S.misc[M_BIT] = m & 3;
+      }
+      __syncthreads();
+      const int lo = S.misc[M_LO], hi = S.misc[M_HI], m = S.misc[M_BIT];
+      double e;
+      if (lo > hi) {  // L maps to a multiple of the identity
+        e = m == 0 ? 1.0 : (m == 2 ? -1.0 : 0.0);
+      } else {
+        const int c0 = S.misc[M_CENTER];
+        const int tgt = c0 < lo ? lo : (c0 > hi ? hi : c0);
+        if (tgt != c0) mps_move_center<T>(P, S, shot, X, tgt);
+        e = S.misc[M_FAIL] ? nan("") : mps_expect<T>(P, S, shot, X, lo, hi, m);
+      }
+      if (tid() == 0) out[shot] = e;
+    } else {
+      mps_move_center<T>(P, S, shot, X, cut);
+      const int l = S.chi[cut], r = S.chi[cut + 1], mrows = 2 * l, kx = min(mrows, r);
+      int cnt = 0;
+      if (!S.misc[M_FAIL] && mrows <= kMaxVec) {
+        const cplx<T> *A = site_ptr<T>(P, shot, cut);
+        for (int e = tid(); e < mrows * r; e += kThreads) X.y[e] = A[e];
+        __syncthreads();
+        qr_r_inplace<T>(mrows, r, X.y, r, S.jbuf, P.svd_elems, S.red, S.dmisc + 4);
+        // Jacobi on R^dag (r x kx, column-major, ld r), in place as in the sweep
+        for (int e = tid(); e < r * kx; e += kThreads) X.y[e] = cconj(X.y[e]);
+        __syncthreads();
+        svd_onesided_blocked<T>(r, kx, X.y, nullptr, X.lam, &S.misc[M_JFLAG], S.red, S.jbuf, P.svd_elems,
+                                sizeof(T) == 4 && kx > 16 && r <= kThreads ? reinterpret_cast<float *>(S.lam)
+                                                                            : nullptr);
+        sort_desc<T>(kx, X.lam, S.perm);
+        for (int i = tid(); i < kx; i += kThreads) out[i] = fmax(static_cast<double>(X.lam[S.perm[i]]), 0.0);
+        cnt = kx;
+      }
+      if (tid() == 0) *count = cnt;
+    }
+    __syncthreads();
+    for (int e = tid(); e <= n; e += kThreads) P.chi[shot * (n + 1) + e] = S.chi[e];
+    if (tid() == 0) {
+      P.center[shot] = S.misc[M_CENTER];
+      if (S.misc[M_FAIL]) P.status[shot] = S.misc[M_FAIL];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// <mu| phase (x)_k op_k |phi> of two MPSs over all n sites: mu is the shot's
+// own MPS (bonds S.chi), phi a stored state (sites at site_off in phi, bonds
+// phi_chi).  The Pauli string in S.ppx/ppz (letters X^x Z^z) acts on phi when
+// with_op.  Transfer matrices E (chi_mu x chi_phi): E <- A_mu^dag (E B),
+// through two GEMMs per site.  CTA-wide; returns the complex value in double.
+template <typename T>
+static __device__ cplx<double> mps_overlap(const EngineParams &P, const Smem<T> &S, int64_t shot, const Scratch<T> &X,
+                                           const cplx<T> *phi, const int *phi_chi, bool with_op, int m) {
+  const int n = P.n;
+  const cplx<T> one = cmake<T>(1, 0), zero = cmake<T>(0, 0);
+  MpoSpec<T> sp;
+  sp.kind = MPO_ROT; sp.lo = -1; sp.hi = -1; sp.j = -1;
+  sp.w0 = one; sp.w1 = one; sp.v0 = zero; sp.v1 = zero;
+  for (int k = 0; k < n; ++k) {
+    const cplx<T> *A = site_ptr<T>(P, shot, k);
+    const int clm = S.chi[k], crm = S.chi[k + 1];
+    const int clp = phi_chi[k], crp = phi_chi[k + 1];
+    const cplx<T> *B = phi + P.site_off[k];
+    const bool acts = with_op && (((S.ppx[k >> 6] | S.ppz[k >> 6]) >> (k & 63)) & 1);
+    if (acts) {
+      cplx<T> op[4];
+      site_op(sp, S.ppx, S.ppz, k, 1, op);
+      const int64_t tot = static_cast<int64_t>(clp) * 2 * crp;
+      for (int64_t e = tid(); e < tot; e += kThreads) {
+        const int r = static_cast<int>(e % crp), s2 = static_cast<int>((e / crp) % 2);
+        const int64_t l = e / (2 * crp);
+        cplx<T> v = zero;
+        cfma(v, op[s2 * 2 + 0], B[(l * 2 + 0) * crp + r]);
+        cfma(v, op[s2 * 2 + 1], B[(l * 2 + 1) * crp + r]);
+        X.sa[e] = v;
+      }
+      __syncthreads();
+      B = X.sa;
+    }
+    if (k == 0) {  // E = A_mu^dag B over the physical index (chi_0 = 1)
+      cgemm<T, 1, 0>(crm, crp, 2 * clm, one, A, crm, B, crp, zero, X.e, crp, S.tile);
+    } else {
+      cgemm<T, 0, 0>(clm, 2 * crp, clp, one, X.e, clp, B, 2 * crp, zero, X.te, 2 * crp, S.tile);
+      cgemm<T, 1, 0>(crm, crp, 2 * clm, one, A, crm, X.te, crp, zero, X.e, crp, S.tile);
+    }
+  }
+  const cplx<T> v = X.e[0];
+  cplx<double> r = cmake<double>(static_cast<double>(v.re), static_cast<double>(v.im));
+  const cplx<double> ph = ipow<double>(m);
+  r = cmul(ph, r);
+  __syncthreads();
+  return r;
+}
+
+// Backward pass of the adjoint (see stn_logprob_grad): one CTA per record,
+// the shot's MPS holding mu (initially the final state of the forced forward
+// pass), the ops walked from last to first.  At a rotation of pair k the term
+// 2 Re <mu| (-i P') |phi_j> / <mu|phi_j> is added to grad[k] (phi_j the
+// stored state after that rotation), then mu <- exp(+i theta P') mu; a case-A
+// measurement applies its projector again, a case-B measurement applies
+// U |v><0|_j; every application is followed by the truncating sweep.
+// Clifford gates and Paulis only changed the frame and leave mu alone.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(EngineParams P, double *grad) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const int n = P.n, W = P.W;
+  Smem<T> S = carve<T>(smem_raw, n, W, P.svd_elems);
+  Scratch<T> X = scratch_for<T>(P, P.work_c);
+  for (int64_t shot = blockIdx.x; shot < P.shots; shot += gridDim.x) {
+    for (int e = tid(); e <= n; e += kThreads) S.chi[e] = P.chi[shot * (n + 1) + e];
+    if (tid() == 0) {
+      S.misc[M_CENTER] = P.center[shot];
+      S.misc[M_FAIL] = P.status[shot];
+      S.misc[M_MAXCHI] = P.maxchi[shot];
+      S.dmisc[D_DISC] = 0.0;
+      S.dmisc[D_FLOPS] = 0.0;
+    }
+    __syncthreads();
+    for (int oi = P.n_ops_total - 1; oi >= 0 && !S.misc[M_FAIL]; --oi) {
+      const Op op = P.ops[oi];
+      if (op.kind != OP_ROT && op.kind != OP_MEAS) continue;
+      const int64_t t = shot * P.n_ops_total + oi;
+      const int32_t *ti = P.tape_info + t * kTapeInts;
+      const int info = ti[0], lo = ti[1], hi = ti[2], jq = ti[3];
+      const int m = info & 3;
+      if (tid() < W) {
+        S.ppx[tid()] = P.tape_px[t * W + tid()];
+        S.ppz[tid()] = P.tape_pz[t * W + tid()];
+      }
+      __syncthreads();
+      MpoSpec<T> &sp = *S.spec;
+      if (op.kind == OP_ROT) {
+        const int64_t slot = shot * P.n_rot + P.rot_ord[oi];
+        const cplx<T> *phi = reinterpret_cast<const cplx<T> *>(P.phi_store) + slot * P.slab_elems;
+        const int *phi_chi = P.phi_chi + slot * (n + 1);
+        const cplx<double> num = mps_overlap<T>(P, S, shot, X, phi, phi_chi, true, m + 3);  // (-i) i^m
+        const cplx<double> den = mps_overlap<T>(P, S, shot, X, phi, phi_chi, false, 0);
+        if (tid() == 0) {
+          const double d2 = den.re * den.re + den.im * den.im;
+          const double re = (num.re * den.re + num.im * den.im) / d2;  // Re(num / den)
+          if (!(d2 > 0.0) || !isfinite(re)) S.misc[M_FAIL] = STN_ENUMERIC;
+          else atomicAdd(&grad[op.idx], 2.0 * re);
+          const double th = P.theta[op.idx];
+          sp.kind = MPO_ROT;
+          sp.lo = lo; sp.hi = hi; sp.j = -1;
+          sp.w0 = cmake<T>(static_cast<T>(cos(th)), 0);
+          sp.w1 = cmul(cmake<T>(0, static_cast<T>(sin(th))), ipow<T>(m));  // +i sin(theta) i^m
+        }
+      } else if (tid() == 0) {
+        const int caseB = (info >> 2) & 1, bit = (info >> 3) & 1, lidx = (info >> 4) & 3, neg = (info >> 6) & 1;
+        sp.lo = lo; sp.hi = hi; sp.j = jq;
+        sp.w0 = cmake<T>(1, 0);
+        sp.w1 = cmake<T>(1, 0);
+        if (!caseB) {  // the forward projector (I + (-1)^b P')/2 again
+          const int sgn = (bit ? -1 : 1) * ((m & 2) ? -1 : 1);
+          sp.kind = MPO_PROJ_Z;
+          sp.par = sgn > 0 ? 0 : 1;
+        } else {  // U |v><0|_j, v the lambda eigenvector of the site-j letter
+          (void)neg;
+          const T r2 = static_cast<T>(0.70710678118654752440);
+          const bool zj = lidx >= 2;
+          const bool lam_neg = lidx & 1;
+          sp.kind = MPO_ADJ_B;
+          sp.v0 = cmake<T>(r2, 0);
+          sp.v1 = zj ? cmake<T>(0, lam_neg ? -r2 : r2) : cmake<T>(lam_neg ? -r2 : r2, 0);
+        }
+      }
+      __syncthreads();
+      if (S.misc[M_FAIL]) break;
+      const int c0 = S.misc[M_CENTER];
+      const int tgt = c0 < lo ? lo : (c0 > hi ? hi : c0);
+      if (tgt != c0) mps_move_center<T>(P, S, shot, X, tgt);
+      if (S.misc[M_FAIL]) break;
+      mps_prepare<T>(P, S, shot, X, lo, hi);
+      __syncthreads();
+      mps_finish<T>(P, S, shot, X, lo, hi);
+      __syncthreads();
+    }
+    for (int e = tid(); e <= n; e += kThreads) P.chi[shot * (n + 1) + e] = S.chi[e];
+    if (tid() == 0) {
+      P.center[shot] = S.misc[M_CENTER];
+      P.status[shot] = S.misc[M_FAIL];
+      if (S.misc[M_FAIL]) atomicCAS(P.err, 0, S.misc[M_FAIL]);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+cudaError_t launch_adjoint_t(const EngineParams &p, double *grad, int grid, cudaStream_t s) {
+  size_t smem = smem_bytes<T>(p.n, p.W, p.svd_elems);
+  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  adjoint_kernel<T><<<grid, kThreads, smem, s>>>(p, grad);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_diag_t(const EngineParams &p, int what, int target, int cut, const int32_t *lq, int nl,
+                          int letter, double *out, int *count, int grid, cudaStream_t s) {
+  size_t smem = smem_bytes<T>(p.n, p.W, p.svd_elems);
+  cudaError_t e = cudaFuncSetAttribute(diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  diag_kernel<T><<<grid, kThreads, smem, s>>>(p, what, target, cut, lq, nl, letter, out, count);
   return cudaGetLastError();
 }
 

@@ -195,4 +195,18 @@ def wilson_interval(k, n, z=1.959963984540054):
     den = 1 + z * z / n
     c = (ph + z * z / (2 * n)) / den
     h = z * np.sqrt(ph * (1 - ph) / n + z * z / (4 * n * n)) / den
-    return max(0.0, c - h), min(1.0, c + h)
+    lo = 0.0 if k == 0 else max(0.0, c - h)  # exact ends (no rounding residue)
+    hi = 1.0 if k == n else min(1.0, c + h)
+    return lo, hi
+
+
+def eq1_estimate(expectations, corrections):
+    """P_L of Sec. II, Eq. 1: the mean over the sampled syndromes of
+    |sin(theta_i / 2)|, with sin^2(theta_i / 2) = (1 - (-1)^c_i <L>_i) / 2
+    from the logical expectation <L>_i before the readout
+    (stn_logical_expectation) and the decoder's correction c_i.  For Pauli
+    errors <L>_i = +-1 and the estimate is the sampled failure rate."""
+    e = np.asarray(expectations, dtype=np.float64)
+    c = np.asarray(corrections, dtype=np.float64)
+    q = np.clip(0.5 * (1.0 - (-1.0) ** c * e), 0.0, 1.0)
+    return float(np.mean(np.sqrt(q)))

@@ -77,6 +77,14 @@ def test_lookup_decoder_on_single_faults():
 
 def test_wilson_interval():
     lo, hi = wilson_interval(0, 100)
-    assert abs(lo) < 1e-12 and abs(hi - 0.03699) < 1e-4
+    assert lo == 0.0 and abs(hi - 0.03699) < 1e-4
     lo, hi = wilson_interval(50, 100)
     assert abs(lo - 0.40383) < 1e-4 and abs(hi - 0.59617) < 1e-4
+
+
+def test_eq1_estimate_reduces_to_failure_rate_for_pauli_errors():
+    from paper_2605_29514_gb300.decoder import eq1_estimate
+    e = np.array([1.0, -1.0, 1.0, -1.0])
+    c = np.array([0, 1, 1, 0])
+    assert eq1_estimate(e, c) == 0.5  # shots 2 and 3 fail
+    assert abs(eq1_estimate([np.cos(0.4)], [0]) - np.sin(0.2)) < 1e-15

@@ -20,24 +20,28 @@ from workloads import D3_EXACT, theta_table
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_d3_1000_records.txt")
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
-def test_d3_logical_error_rate_matches_oracle():
+@pytest.mark.parametrize("name,basis", [("oracle_d3_1000_records.txt", "Z"), ("oracle_d3x_400_records.txt", "X")])
+def test_d3_logical_error_rate_matches_oracle(name, basis):
+    """Z-memory (the configuration: ZZ crosstalk makes only Z-type errors,
+    which cannot flip Z_L, so its rate is zero on both sides) and the same
+    circuit as an X-memory, where they flip X_L."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    if not os.path.exists(GOLDEN):
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
         pytest.skip("golden records not generated")
     stn.build()
-    w = D3_EXACT
+    w = D3_EXACT.with_(memory_basis=basis)
     ref = {}
-    for line in open(GOLDEN):
+    for line in open(path):
         if line.startswith("#"):
             continue
         s, bits, near = line.split()
         ref[int(s)] = ([int(c) for c in bits], int(near))
     shots = len(ref)
-    assert shots == w.shots
     sim = stn.Simulator(w, max_shots=shots)
     theta = theta_table(w, sim.n_pairs)
     out = sim.sample_shots(shots, 0, theta)

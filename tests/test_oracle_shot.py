@@ -377,3 +377,42 @@ def test_x_memory_and_schedule_match_dense_statevector():
         r = run_shot(w, shot, th, prog)
         assert r.record == rec
         assert np.max(np.abs(np.array(born) - np.array(r.born))) < 1e-11
+
+
+# -- the adjoint gradient of log P(record) (oracle.adjoint) -------------------
+def test_adjoint_single_rotation_closed_form():
+    """|+>|0>, exp(-i theta Z Z), H, measure qubit 0: P(1) = sin^2 theta, so
+    d/dtheta log P(1) = 2 cot theta and d/dtheta log P(0) = -2 tan theta."""
+    from oracle import adjoint
+    ops = [("H", 0), ("ROT", 0), ("H", 0), ("M", 0, 0, 1, 0, False, -1)]
+    prog = tiny_program(2, ops, [Pair(0, 1, "ZZ", 0)])
+    w = D3_EXACT.with_(p=0.0, chi_cap=64)
+    for theta in (0.1, 0.4):
+        for bit, want in ((1, 2.0 / math.tan(theta)), (0, -2.0 * math.tan(theta))):
+            lp, g = adjoint.logprob_and_grad(w, 0, [theta], [bit], prog)
+            p = math.sin(theta) ** 2 if bit else math.cos(theta) ** 2
+            assert abs(lp - math.log(p)) < 1e-13
+            assert abs(g[0] - want) < 1e-12 * max(1.0, abs(want))
+
+
+@pytest.mark.parametrize("basis", ["Z", "X"])
+def test_adjoint_matches_central_differences(basis):
+    """Whole d = 3 shots (2 rounds, noise, quenched angles), nothing
+    truncated: the adjoint gradient of the forced-record log-likelihood equals
+    central differences with h = 1e-4 on every pair."""
+    from oracle.adjoint import forced_logprob, logprob_and_grad
+    w = D3_EXACT.with_(rounds=2, chi_cap=256, svd_cutoff=1e-14, degeneracy_tol=0.0, p=0.01, theta=0.2,
+                       memory_basis=basis)
+    if basis == "X":
+        w = w.with_(rounds=1)
+    prog = make_program(w)
+    th = theta_table(w.with_(theta_sigma=0.05), len(prog.pairs))
+    rec = run_shot(w, 3, th, prog).record
+    lp, g = logprob_and_grad(w, 3, th, rec, prog)
+    h = 1e-4
+    for k in range(0, len(th), 3):
+        tp, tm = th.copy(), th.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (forced_logprob(w, 3, tp, rec, prog) - forced_logprob(w, 3, tm, rec, prog)) / (2 * h)
+        assert abs(g[k] - fd) < 1e-6 * max(1.0, abs(fd)), (k, g[k], fd)
