@@ -42,7 +42,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import D5_BENCH, PRECISION_C128, theta_table  # noqa: E402
+from workloads import D5_BENCH, PRECISION_C128, PRECISION_C64_SVD64, theta_table  # noqa: E402
 
 METRIC = "shots/s of d=5, 5-round crosstalk syndrome extraction on 1 GB300 at <=1e-5 Born error"
 GOLDEN_D5 = os.path.join(ROOT, "tests", "golden", "oracle_d5_records.txt")
@@ -59,8 +59,9 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chi-cap", type=int, default=None,
                     help="override the bond cap (smaller profiling captures only; not a bench line)")
-    ap.add_argument("--precision", default="c64", choices=["c64", "c128"],
-                    help="c128: the plain per-shot complex128 GPU path on the same workload (comparator)")
+    ap.add_argument("--precision", default="c64", choices=["c64", "c128", "c64-svd64"],
+                    help="c128: the plain per-shot complex128 GPU path on the same workload (comparator); "
+                         "c64-svd64: complex64 contractions with every bond SVD in FP64")
     ap.add_argument("--dense-routines", action="store_true",
                     help="time the truncation sweep's dense routines alone on one CTA and exit")
     return ap.parse_args(argv)
@@ -342,6 +343,8 @@ def main():
     if args.precision == "c128":
         w = w.with_(precision=PRECISION_C128, svd_cutoff=1e-12, degeneracy_tol=1e-12,
                     name=w.name.replace("_c64", "_c128"))
+    elif args.precision == "c64-svd64":
+        w = w.with_(precision=PRECISION_C64_SVD64, name=w.name + "_svd64")
     if args.impl == "reference":
         reference_arm(args, w)
         return
@@ -433,6 +436,10 @@ def main():
                                 "jacobi_sweeps_per_large_svd": dprof["jacobi_sweeps_large"]
                                 / max(1.0, dprof["svd_count_large"])},
               "source": "stn_profile_counters: SM clock cycles of each CTA per phase over the timed steps"}
+    if clk and clk.get("sm_mhz"):
+        # cycles the CTAs spent in their op loops over the cycles the launches
+        # held the SMs: below 1 when a launch waits for its slowest shot
+        phases["sm_busy_fraction"] = round(dprof["op_loop_cycles"] / (min(B, sms) * kernel_s * clk["sm_mhz"] * 1e6), 4)
     if pg:
         t = torch.tensor([secs, host_s, kernel_s], dtype=torch.float64, device="cuda")
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
@@ -470,7 +477,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": ws, "steps": K, "warmup": W,
                 "ms_per_step": 1000.0 * secs / K, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "c64" if w.precision else "c128", "data": "synthetic",
+                "vs_baseline": None, "dtype": {0: "c128", 1: "c64", 2: "c64+f64svd"}[w.precision], "data": "synthetic",
                 "config": {"workload": w.name, "distance": w.distance, "rounds": w.rounds, "theta": w.theta,
                            "p": w.p, "chi_cap": w.chi_cap, "shots_per_batch_per_rank": B,
                            "step": "one layer step over the batch: CNOT layer l of round r with its crosstalk "

@@ -52,7 +52,13 @@ typedef enum {
 } stn_status;
 
 enum { STN_PAIRS_ADJACENT_IDLE = 0, STN_PAIRS_ADJACENT_IDLE_DIAG_XX = 1 };
-enum { STN_PRECISION_C128 = 0, STN_PRECISION_C64 = 1 };
+/* Arithmetic of the MPS path.  C128: complex128 throughout.  C64: complex64
+ * contractions; norms, Born probabilities and log P in double; the SVDs of
+ * bonds whose complex128 copy fits shared memory (about 75 columns) in double
+ * precision, larger bonds by single-precision Jacobi on the R factor.
+ * C64_SVD64: as C64 with every bond SVD (R factor and Jacobi) in double
+ * precision, at the FP64 rate of the GPU. */
+enum { STN_PRECISION_C128 = 0, STN_PRECISION_C64 = 1, STN_PRECISION_C64_SVD64 = 2 };
 enum { STN_BASIS_Z = 0, STN_BASIS_X = 1 };
 enum { STN_LAYERS_IDLE = 0xFF }; /* pair_layer_mask entry: use the idle rule */
 
@@ -182,6 +188,20 @@ stn_status stn_apply_round_device(stn_ctx *ctx, int32_t round, const double *d_t
  * Asynchronous.  Errors: STN_EINVAL for a bad step or no batch. */
 int32_t stn_num_steps(const stn_ctx *ctx);
 stn_status stn_apply_step_device(stn_ctx *ctx, int32_t step, const double *d_theta);
+
+/* A whole batch as one CUDA graph (the persistent scheduler's launches
+ * captured once and replayed): stn_capture_batch records, on the context's
+ * stream (it must not be the legacy default stream), the batch start and one
+ * launch per layer step for `shots` shots with the angles d_theta[K] (device,
+ * read at replay, so the caller may change their values between replays);
+ * stn_launch_captured replays it for the global shots shot_offset..
+ * shot_offset + shots - 1, equivalent to stn_begin_batch followed by every
+ * layer step.  Asynchronous; results are read with stn_read_records as
+ * usual.  The shot offset is copied from the context (host) to the device
+ * before each replay.  Errors: STN_EINVAL (no capture yet, bad shots, the
+ * default stream), STN_ECUDA. */
+stn_status stn_capture_batch(stn_ctx *ctx, int64_t shots, const double *d_theta);
+stn_status stn_launch_captured(stn_ctx *ctx, uint64_t shot_offset);
 
 /* Wait for the stream and report any device-side failure of the batch. */
 stn_status stn_sync(stn_ctx *ctx);

@@ -141,6 +141,17 @@ class Simulator:
     def apply_step_device(self, step, d_theta_ptr):
         self._check(self.lib.stn_apply_step_device(self.ctx, int(step), ctypes.c_void_p(d_theta_ptr)))
 
+    def capture_batch(self, shots, d_theta_ptr):
+        """Capture a whole batch (batch start and every layer step) as one
+        CUDA graph (stn_capture_batch); the simulator needs its own stream."""
+        self._check(self.lib.stn_capture_batch(self.ctx, int(shots), ctypes.c_void_p(d_theta_ptr)))
+        self._graph_shots = int(shots)
+
+    def launch_captured(self, shot_offset):
+        """Replay the captured batch for global shots shot_offset.. ."""
+        self._check(self.lib.stn_launch_captured(self.ctx, int(shot_offset)))
+        self.shots = self._graph_shots
+
     def sync(self):
         self._check(self.lib.stn_sync(self.ctx))
 

@@ -105,6 +105,8 @@ EXPORTS = [
     ("stn_num_steps", ctypes.c_int32, [ctypes.c_void_p]),
     ("stn_apply_step_device", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     ("stn_sync", ctypes.c_int, [ctypes.c_void_p]),
+    ("stn_capture_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    ("stn_launch_captured", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     ("stn_read_records", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p]),
     ("stn_device_records", ctypes.c_void_p, [ctypes.c_void_p]),

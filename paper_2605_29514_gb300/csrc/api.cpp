@@ -42,6 +42,9 @@ struct stn_ctx {
   int32_t *d_det_table = nullptr, *d_logical = nullptr;
   void *d_scratch = nullptr;
   int *d_err = nullptr;
+  uint64_t *d_offset = nullptr;  // shot offset read by captured graphs
+  cudaGraphExec_t graph = nullptr;
+  int64_t graph_shots = 0;
   double *d_diag = nullptr;     // diagnostics output: max(max_shots, 512) doubles
   int *d_diag_count = nullptr;
   int32_t *d_diag_q = nullptr;  // n qubit indices
@@ -115,6 +118,7 @@ stn::EngineParams params(const stn_ctx *c, int op_begin, int op_end, const doubl
   p.g_elems = c->plan.g_elems;
   p.work_c = c->plan.work_c;
   p.svd_elems = c->svd_elems;
+  p.svd64_all = c->cfg.precision == STN_PRECISION_C64_SVD64 ? 1 : 0;
   p.err = c->d_err;
   return p;
 }
@@ -122,8 +126,9 @@ stn::EngineParams params(const stn_ctx *c, int op_begin, int op_end, const doubl
 std::string validate(const stn_config *cfg) {
   if (!cfg) return "config is NULL";
   if (cfg->chi_cap < 1 || cfg->chi_cap > 256) return "chi_cap must be 1..256";
-  if (cfg->precision != STN_PRECISION_C128 && cfg->precision != STN_PRECISION_C64)
-    return "precision must be STN_PRECISION_C128 or STN_PRECISION_C64";
+  if (cfg->precision != STN_PRECISION_C128 && cfg->precision != STN_PRECISION_C64 &&
+      cfg->precision != STN_PRECISION_C64_SVD64)
+    return "precision must be one of STN_PRECISION_*";
   const double rates[5] = {cfg->p, cfg->p1_scale, cfg->p2_scale, cfg->pR_scale, cfg->pM_scale};
   for (double r : rates)
     if (!(r >= 0.0) || !std::isfinite(r)) return "noise rates must be finite and >= 0";
@@ -311,6 +316,7 @@ stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_strea
   A(dalloc(c, &c->d_logical, sizeof(int32_t) * c->prog.logical.size()));
   A(dalloc(c, &c->d_scratch, c->elem * static_cast<size_t>(c->grid) * c->plan.total));
   A(dalloc(c, &c->d_err, sizeof(int)));
+  A(dalloc(c, &c->d_offset, sizeof(uint64_t)));
   A(dalloc(c, &c->d_diag, sizeof(double) * std::max<int64_t>(S, 512)));
   A(dalloc(c, &c->d_diag_count, sizeof(int)));
   A(dalloc(c, &c->d_diag_q, sizeof(int32_t) * n));
@@ -348,6 +354,7 @@ stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_strea
 void stn_destroy(stn_ctx *c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
   for (void *p : c->allocs) cudaFree(p);
   delete c;
 }
@@ -632,6 +639,56 @@ stn_status stn_schmidt_values(stn_ctx *c, int64_t shot, int32_t cut, double *h_s
     e = cudaMemcpy(h_sig2, c->d_diag, sizeof(double) * cnt, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(c, e, "stn_schmidt_values");
   *h_count = cnt;
+  return STN_OK;
+}
+
+stn_status stn_capture_batch(stn_ctx *c, int64_t shots, const double *d_theta) {
+  if (!c) return STN_EINVAL;
+  if (!c->stream) return fail(c, STN_EINVAL, "graph capture needs the context's own (non-default) stream");
+  if (shots < 1 || shots > c->max_shots) return fail(c, STN_EINVAL, "shots must be 1..max_shots");
+  if (!d_theta && c->K > 0) return fail(c, STN_EINVAL, "theta is NULL");
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->shots = shots;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+  stn::EngineParams p = params(c, 0, 0, d_theta ? d_theta : c->d_theta);
+  p.shot_offset_dev = c->d_offset;
+  cudaError_t le = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+  if (le == cudaSuccess) le = stn::launch_init(c->cfg.precision, p, c->stream);
+  const int grid = static_cast<int>(std::min<int64_t>(c->grid, shots));
+  for (size_t st = 0; le == cudaSuccess && st + 1 < c->prog.step_begin.size(); ++st) {
+    p.op_begin = c->prog.step_begin[st];
+    p.op_end = c->prog.step_begin[st + 1];
+    le = stn::launch_round(c->cfg.precision, p, grid, c->stream);
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(c->stream, &g);
+  if (le != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(c, le != cudaSuccess ? le : e, "capture");
+  }
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    return cuda_fail(c, e, "graph instantiate");
+  }
+  c->graph_shots = shots;
+  return STN_OK;
+}
+
+stn_status stn_launch_captured(stn_ctx *c, uint64_t shot_offset) {
+  if (!c) return STN_EINVAL;
+  if (!c->graph) return fail(c, STN_EINVAL, "no captured batch: call stn_capture_batch first");
+  c->shots = c->graph_shots;
+  c->shot_offset = shot_offset;
+  cudaError_t e = cudaMemcpyAsync(c->d_offset, &c->shot_offset, sizeof(uint64_t), cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e == cudaSuccess) e = cudaGraphLaunch(c->graph, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
   return STN_OK;
 }
 

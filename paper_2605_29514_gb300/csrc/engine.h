@@ -31,6 +31,7 @@ struct EngineParams {
   double cutoff, delta;
   double p1, p2, pR, pM;
   uint64_t seed, shot_offset;
+  const uint64_t *shot_offset_dev;  // when set, the offset is read here (captured graphs)
   int shots;
   // frame: inverse tableau rows X_0..X_{n-1}, Z_0..Z_{n-1}
   uint64_t *tab_x, *tab_z;  // [shot][2n][W]
@@ -53,6 +54,7 @@ struct EngineParams {
   int64_t scratch_elems, ap_elems, g_elems;
   int work_c;               // largest bond of the plan (sizes the work area)
   int svd_elems;            // complex elements of the shared-memory SVD buffer
+  int svd64_all;            // complex64 path: every bond SVD in double precision
   int *err;                 // first error code seen on the device
   // Adjoint of log P(record) (all null in an ordinary run).  forced: records
   // to reproduce, [shot][rec_bytes]; a measurement's outcome is then its

@@ -1586,6 +1586,38 @@ static __device__ void mps_finish(const EngineParams &P, const Smem<T> &S, int64
       for (int i = tid(); i < n2; i += kThreads) X.lam[i] = static_cast<T>(sd[i]);
       __syncthreads();
       Vc = X.v;
+    } else if (sizeof(T) == 4 && P.svd64_all) {
+      // Complex64 contractions with every SVD in double precision: the large
+      // path (Householder R factor, Jacobi on R^dag) on a complex128 copy of
+      // C in the scratch areas h and v (contiguous, 4 c^2 complex128), with
+      // the shared buffer as complex128 staging; the rotated columns come back
+      // in single precision.
+      if (r > kMaxVec) {
+        if (tid() == 0) S.misc[M_FAIL] = STN_EOVERFLOW;
+        __syncthreads();
+        return;
+      }
+      cplx<double> *Cd = reinterpret_cast<cplx<double> *>(X.h);
+      cplx<double> *jd = reinterpret_cast<cplx<double> *>(S.jbuf);
+      double *sd = reinterpret_cast<double *>(X.te);
+      for (int e = tid(); e < r * n2; e += kThreads)
+        Cd[e] = cmake<double>(static_cast<double>(X.y[e].re), static_cast<double>(X.y[e].im));
+      __syncthreads();
+      const long long tqr = clock64();
+      qr_r_inplace<double>(r, n2, Cd, n2, jd, P.svd_elems / 2, S.red, S.dmisc + 4);
+      if (tid() == 0) S.dmisc[D_PROF + 1 + PROF_SVD_QR] += static_cast<double>(clock64() - tqr);
+      const int kx = min(r, n2);
+      for (int e = tid(); e < n2 * kx; e += kThreads) Cd[e] = cconj(Cd[e]);
+      __syncthreads();
+      const int sweeps = svd_onesided_blocked<double>(n2, kx, Cd, nullptr, sd, &S.misc[M_JFLAG], S.red, jd,
+                                                      P.svd_elems / 2);
+      if (tid() == 0) S.dmisc[D_PROF + 1 + PROF_JSWEEPS] += sweeps;
+      for (int e = tid(); e < n2 * kx; e += kThreads)
+        X.y[e] = cmake<T>(static_cast<T>(Cd[e].re), static_cast<T>(Cd[e].im));
+      for (int i = tid(); i < n2; i += kThreads) X.lam[i] = i < kx ? static_cast<T>(sd[i]) : T(0);
+      __syncthreads();
+      Vc = X.y;
+      vec_from_columns = true;
     } else if (in_smem) {
       for (int e = tid(); e < r * n2; e += kThreads) {
         int i = e / n2, j = e % n2;
@@ -1913,7 +1945,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
     }
     __syncthreads();
     long long t_ops = clock64();
-    const uint64_t gshot = P.shot_offset + static_cast<uint64_t>(shot);
+    const uint64_t gshot = (P.shot_offset_dev ? *P.shot_offset_dev : P.shot_offset) + static_cast<uint64_t>(shot);
     for (int oi = P.op_begin; oi < P.op_end; ++oi) {
       if (S.misc[M_FAIL]) break;
       const Op op = P.ops[oi];

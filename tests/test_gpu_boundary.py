@@ -106,3 +106,22 @@ def test_layer_steps_equal_rounds():
     out = sim.read_records()
     for key in ("records", "born", "max_chi", "logp", "discarded"):
         assert np.array_equal(out[key], base[key]), key
+
+
+def test_captured_batch_replays_equal_plain_batches():
+    """A batch captured once as a CUDA graph and replayed for two shot
+    offsets gives the records and Born probabilities of plain batches."""
+    w = D3_EXACT.with_(p=0.02, rounds=2)
+    shots = 5
+    stream = torch.cuda.Stream()
+    sim = stn.Simulator(w, max_shots=shots, stream=stream.cuda_stream)
+    theta = theta_table(w, sim.n_pairs)
+    d_theta = torch.tensor(theta, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    sim.capture_batch(shots, d_theta.data_ptr())
+    for offset in (0, 1000):
+        sim.launch_captured(offset)
+        got = sim.read_records()
+        _, ref, _ = gpu_run(w, shots, offset, theta)
+        assert np.array_equal(got["records"], ref["records"])
+        assert np.array_equal(got["born"], ref["born"])

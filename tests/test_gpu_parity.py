@@ -231,3 +231,19 @@ def test_mps_stays_canonical(precision):
         for a in sites:
             env = np.einsum("ac,asb,csd->bd", env, a.conj(), a)
         assert abs(env[0, 0].real - 1.0) < 10 * tol, f"shot {s}: norm {env[0, 0].real}"
+
+
+def test_complex64_with_fp64_svds_parity():
+    """complex64 contractions with every bond SVD in double precision
+    (STN_PRECISION_C64_SVD64), d=3 at theta = 0.2 with bonds past the
+    shared-memory limit (cap 64): Born within 1e-5 of the oracle, records
+    identical up to near-threshold draws."""
+    from workloads import PRECISION_C64_SVD64
+    w = D3_EXACT.with_(precision=PRECISION_C64_SVD64, svd_cutoff=D5_BENCH.svd_cutoff,
+                       degeneracy_tol=D5_BENCH.degeneracy_tol, theta=0.2, rounds=2)
+    shots = 6
+    sim, out, theta = gpu_run(w, shots)
+    prog = make_program(w)
+    for s in range(shots):
+        ref = run_shot(w, s, theta, prog)
+        compare_shot(sim, out, s, ref, 1e-5, check_tableau=False)

@@ -14,7 +14,8 @@ from dataclasses import dataclass, replace
 import numpy as np
 
 PRECISION_C128 = 0  # complex128 contractions, FP64 SVD
-PRECISION_C64 = 1  # complex64 contractions, FP64 scalars
+PRECISION_C64 = 1  # complex64 contractions, FP64 scalars and small-bond SVDs
+PRECISION_C64_SVD64 = 2  # complex64 contractions, every bond SVD in FP64
 
 
 @dataclass(frozen=True)
