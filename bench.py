@@ -3,7 +3,8 @@ on one GB300 (theta = 0.10 ZZ on idle adjacent pairs, depolarising p = 1e-3
 with the Table I ratios, chi cap 256, complex64 contractions).
 
 A step is one layer step of the program (stn_apply_step_device) applied to a
-batch of B shots, one launch of the persistent round kernel: CNOT layer l of
+batch of B shots (default two per SM, taken from a queue by one persistent
+CTA per SM), one launch of the round kernel: CNOT layer l of
 syndrome round r with the crosstalk rotations after it, the round's opening
 H gates in its first layer and its closing H gates and ancilla measurements
 in its last, the final data readout in the very last step.  A batch is
@@ -53,7 +54,8 @@ def parse(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--shots", type=int, default=0, help="shots per batch and rank (default: one per SM)")
+    ap.add_argument("--shots", type=int, default=0,
+                    help="shots per batch and rank (default: two per SM, taken from a queue by one CTA per SM)")
     ap.add_argument("--impl", default="stn", choices=["stn", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget per core")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -366,7 +368,7 @@ def main():
     K = max(1, args.steps)
     W = max(3, args.warmup)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    B = args.shots if args.shots > 0 else sms
+    B = args.shots if args.shots > 0 else 2 * sms
     stream = torch.cuda.current_stream()
     peaks = measure_peaks(stn, torch, stream)
     sim = stn.Simulator(w, max_shots=B, stream=stream.cuda_stream)
@@ -485,8 +487,8 @@ def main():
                                    "layer, the final readout in the last step); 4 x 5 = 20 steps = one batch",
                            "counted": counted,
                            "batch_vs_config": f"the configuration's 16,384 shots run as batches of {B} "
-                                              "resident shots (one per SM, one CTA each); every layer step "
-                                              "of a batch is one launch",
+                                              f"resident shots, taken from a queue by {min(B, sms)} persistent "
+                                              "CTAs (one per SM); every layer step of a batch is one launch",
                            "l2": "per-shot MPS state (GBs in all) larger than L2; no flush",
                            "parallelism": f"shots sharded over {ws} rank(s)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -43,6 +43,7 @@ struct stn_ctx {
   void *d_scratch = nullptr;
   int *d_err = nullptr;
   uint64_t *d_offset = nullptr;  // shot offset read by captured graphs
+  int *d_ticket = nullptr;       // shot queue of a round-kernel launch
   cudaGraphExec_t graph = nullptr;
   int64_t graph_shots = 0;
   double *d_diag = nullptr;     // diagnostics output: max(max_shots, 512) doubles
@@ -317,6 +318,7 @@ stn_status stn_create(const stn_config *cfg, int64_t max_shots, void *cuda_strea
   A(dalloc(c, &c->d_scratch, c->elem * static_cast<size_t>(c->grid) * c->plan.total));
   A(dalloc(c, &c->d_err, sizeof(int)));
   A(dalloc(c, &c->d_offset, sizeof(uint64_t)));
+  A(dalloc(c, &c->d_ticket, sizeof(int)));
   A(dalloc(c, &c->d_diag, sizeof(double) * std::max<int64_t>(S, 512)));
   A(dalloc(c, &c->d_diag_count, sizeof(int)));
   A(dalloc(c, &c->d_diag_q, sizeof(int32_t) * n));
@@ -436,7 +438,12 @@ static stn_status launch_ops(stn_ctx *c, int op_begin, int op_end, const double 
   if (!d_theta && c->K > 0) return fail(c, STN_EINVAL, "theta is NULL");
   stn::EngineParams p = params(c, op_begin, op_end, d_theta ? d_theta : c->d_theta);
   int grid = static_cast<int>(std::min<int64_t>(c->grid, c->shots));
-  cudaError_t e = stn::launch_round(c->cfg.precision, p, grid, c->stream);
+  cudaError_t e = cudaSuccess;
+  if (c->shots > grid) {  // more shots than CTAs: take them from a queue
+    e = cudaMemsetAsync(c->d_ticket, 0, sizeof(int), c->stream);
+    p.ticket = c->d_ticket;
+  }
+  if (e == cudaSuccess) e = stn::launch_round(c->cfg.precision, p, grid, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "round kernel");
   return STN_OK;
 }
@@ -659,10 +666,12 @@ stn_status stn_capture_batch(stn_ctx *c, int64_t shots, const double *d_theta) {
   cudaError_t le = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
   if (le == cudaSuccess) le = stn::launch_init(c->cfg.precision, p, c->stream);
   const int grid = static_cast<int>(std::min<int64_t>(c->grid, shots));
+  if (shots > grid) p.ticket = c->d_ticket;
   for (size_t st = 0; le == cudaSuccess && st + 1 < c->prog.step_begin.size(); ++st) {
     p.op_begin = c->prog.step_begin[st];
     p.op_end = c->prog.step_begin[st + 1];
-    le = stn::launch_round(c->cfg.precision, p, grid, c->stream);
+    if (p.ticket) le = cudaMemsetAsync(c->d_ticket, 0, sizeof(int), c->stream);
+    if (le == cudaSuccess) le = stn::launch_round(c->cfg.precision, p, grid, c->stream);
   }
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(c->stream, &g);

@@ -56,6 +56,7 @@ struct EngineParams {
   int svd_elems;            // complex elements of the shared-memory SVD buffer
   int svd64_all;            // complex64 path: every bond SVD in double precision
   int *err;                 // first error code seen on the device
+  int *ticket;              // shot queue of a launch (zeroed before it), or null: grid-stride
   // Adjoint of log P(record) (all null in an ordinary run).  forced: records
   // to reproduce, [shot][rec_bytes]; a measurement's outcome is then its
   // record bit XOR its record-flip event.  With tape_info set, rotations and

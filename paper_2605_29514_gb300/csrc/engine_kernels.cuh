@@ -1214,7 +1214,9 @@ static __device__ Smem<T> carve(char *base, int n, int W, int svd_elems) {
 }
 
 // misc slots
-enum { M_LO = 0, M_HI, M_A, M_B, M_CENTER, M_FAIL, M_KEEP, M_MAXCHI, M_CASEB, M_J, M_BIT, M_LIDX, M_OUTCOME, M_JFLAG };
+// (M_JFLAG + 1 holds the blocked Jacobi's sweep flag; M_TICKET the shot taken from the queue)
+enum { M_LO = 0, M_HI, M_A, M_B, M_CENTER, M_FAIL, M_KEEP, M_MAXCHI, M_CASEB, M_J, M_BIT, M_LIDX, M_OUTCOME, M_JFLAG,
+       M_TICKET = 15 };
 // dmisc slots
 enum { D_DISC = 0, D_LOGP, D_E, D_NORM, D_FLOPS = 8, D_PROF = 8 };  // D_PROF + 1 + ProfSlot
 
@@ -1926,7 +1928,18 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
   const int n = P.n, W = P.W;
   Smem<T> S = carve<T>(smem_raw, n, W, P.svd_elems);
   Scratch<T> X = scratch_for<T>(P, P.work_c);
-  for (int64_t shot = blockIdx.x; shot < P.shots; shot += gridDim.x) {
+  // With a ticket counter the CTAs take the batch's shots in order as they
+  // finish (a work queue that balances uneven shots when the batch holds
+  // more shots than CTAs); without one, shots are grid-strided.
+  for (int64_t it = 0;; ++it) {
+    int64_t shot = blockIdx.x + it * gridDim.x;
+    if (P.ticket) {
+      if (tid() == 0) S.misc[M_TICKET] = atomicAdd(P.ticket, 1);
+      __syncthreads();
+      shot = S.misc[M_TICKET];
+      __syncthreads();
+    }
+    if (shot >= P.shots) break;
     // load the frame and the MPS bookkeeping
     for (int e = tid(); e < 2 * n * W; e += kThreads) {
       S.tx[e] = P.tab_x[shot * 2 * n * W + e];
