@@ -3,8 +3,8 @@ on one GB300 (theta = 0.10 ZZ on idle adjacent pairs, depolarising p = 1e-3
 with the Table I ratios, chi cap 256, complex64 contractions).
 
 A step is one layer step of the program (stn_apply_step_device) applied to a
-batch of B shots (default two per SM, taken from a queue by one persistent
-CTA per SM), one launch of the round kernel: CNOT layer l of
+batch of B shots (default one per SM; a larger batch is taken from a queue by
+one persistent CTA per SM), one launch of the round kernel: CNOT layer l of
 syndrome round r with the crosstalk rotations after it, the round's opening
 H gates in its first layer and its closing H gates and ancilla measurements
 in its last, the final data readout in the very last step.  A batch is
@@ -55,7 +55,7 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--shots", type=int, default=0,
-                    help="shots per batch and rank (default: two per SM, taken from a queue by one CTA per SM)")
+                    help="shots per batch and rank (default: one per SM; more are taken from a queue by one CTA per SM)")
     ap.add_argument("--impl", default="stn", choices=["stn", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget per core")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -368,7 +368,7 @@ def main():
     K = max(1, args.steps)
     W = max(3, args.warmup)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    B = args.shots if args.shots > 0 else 2 * sms
+    B = args.shots if args.shots > 0 else sms
     stream = torch.cuda.current_stream()
     peaks = measure_peaks(stn, torch, stream)
     sim = stn.Simulator(w, max_shots=B, stream=stream.cuda_stream)

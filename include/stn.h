@@ -384,6 +384,20 @@ stn_status stn_dense_svd(int32_t precision, int32_t m, int32_t n, void *d_c, voi
 stn_status stn_dense_svd_noalloc(int32_t precision, int32_t m, int32_t n, const void *d_c, void *d_v,
                                  void *d_sig2, void *cuda_stream);
 
+/* Real GEMM on the tcgen05 tensor cores with FP32 accuracy from TF32
+ * operands (the 3-term split a = a_hi + a_lo: A_hi B_hi + A_hi B_lo +
+ * A_lo B_hi accumulated in FP32 in tensor memory), one CTA, for checking the
+ * tensor-core form of the sweep's contractions (Sec. IV A-B: the MPO and
+ * truncation contractions are products of such matrices, four real ones per
+ * complex one).  d_c (m x n) = d_a (m x k) d_b (k x n), row-major FP32 device
+ * memory, each dimension 1..4096.  *d_status (device int, caller-zeroed) is
+ * set to STN_ETIMEOUT if a bounded wait for the tensor cores ran out (the
+ * kernel then frees its tensor memory and returns).  Asynchronous.
+ * Errors: STN_EINVAL on bad sizes or null pointers, STN_ECUDA on launch
+ * failure. */
+stn_status stn_dense_gemm_tc(int32_t m, int32_t n, int32_t k, const float *d_a, const float *d_b, float *d_c,
+                             int32_t *d_status, void *cuda_stream);
+
 /* Arithmetic-peak probe (the paper has no counterpart: it measures the
  * denominators of the roofline the kernels are placed on).  Launches on
  * `cuda_stream`, on every SM at full occupancy, a kernel of independent

@@ -307,6 +307,15 @@ def philox_uniforms(seed, shot_offset, n_shots, event_offset, n_events, d_out_pt
         raise StnError(st, "stn_philox_uniforms failed")
 
 
+def dense_gemm_tc(m, n, k, d_a, d_b, d_c, d_status, stream=0):
+    """stn_dense_gemm_tc: d_c = d_a @ d_b (row-major FP32) on the tcgen05
+    tensor cores with the 3-term TF32 split."""
+    st = load().stn_dense_gemm_tc(int(m), int(n), int(k), ctypes.c_void_p(d_a), ctypes.c_void_p(d_b),
+                                  ctypes.c_void_p(d_c), ctypes.c_void_p(d_status), ctypes.c_void_p(stream))
+    if st != STN_OK:
+        raise StnError(st, "stn_dense_gemm_tc failed")
+
+
 def peak_probe(kind, iters, stream=0):
     """Launch the arithmetic-peak probe (kind 0 FP32 FMA, 1 FP64 FMA, 2 TF32
     mma.sync) on `stream`; returns the FLOPs it performs.  The caller times
@@ -349,4 +358,4 @@ def dense_svd_noalloc(precision, m, n, d_c, d_v, d_sig2, stream=0):
 
 __all__ = ["Simulator", "StnError", "build", "load", "philox_uniforms", "unpack_records",
            "config_from_workload", "compile_program", "compile_detectors", "dense_qr", "dense_svd",
-           "dense_svd_noalloc", "peak_probe", "layout"]
+           "dense_svd_noalloc", "peak_probe", "layout", "dense_gemm_tc"]

@@ -14,8 +14,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libstn.so")
-SOURCES = ["engine_f32.cu", "engine_f64.cu", "engine.cu", "engine_noalloc.cu", "peaks.cu", "program.cpp",
-           "api.cpp"]
+SOURCES = ["engine_f32.cu", "engine_f64.cu", "engine.cu", "engine_noalloc.cu", "peaks.cu", "tc_gemm.cu",
+           "program.cpp", "api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
@@ -136,6 +136,8 @@ EXPORTS = [
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     ("stn_dense_svd_noalloc", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("stn_dense_gemm_tc", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("stn_peak_probe", ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                       ctypes.c_void_p]),
     ("stn_philox_uniforms", ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,

@@ -120,6 +120,7 @@ stn::EngineParams params(const stn_ctx *c, int op_begin, int op_end, const doubl
   p.work_c = c->plan.work_c;
   p.svd_elems = c->svd_elems;
   p.svd64_all = c->cfg.precision == STN_PRECISION_C64_SVD64 ? 1 : 0;
+  p.use_tc = c->cfg.precision != STN_PRECISION_C128 ? 1 : 0;
   p.err = c->d_err;
   return p;
 }

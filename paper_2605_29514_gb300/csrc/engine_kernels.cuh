@@ -157,12 +157,256 @@ static __device__ double block_sum(double v, double *red) {
   return r;
 }
 
+// ---------------------------------------------------------------------------
+// Complex64 GEMM on the fifth-generation tensor cores (tcgen05).  The CTA's
+// tensor-memory accumulator (128 lanes x 128 FP32 columns: the real part of
+// a 128 x 64 output tile, then its imaginary part), the mbarrier the MMAs
+// complete on and the shared-memory staging area of the operand tiles live
+// in g_tc; a kernel that allocates the accumulator sets enabled.
+//
+// Each product is FP32-accurate from TF32 operands by the 3-term split
+// (Ootomo and Yokota, 2022): x = x_hi + x_lo with both parts TF32, and
+// A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi.  The complex product takes four
+// real ones: Re C = Re A Re B - Im A Im B, Im C = Re A Im B + Im A Re B, so
+// every k step of 8 issues 12 MMAs per part (M = 128, N = 64, K = 8,
+// kind::tf32), accumulated in FP32.  Operand tiles of 128 x 32 (A) and
+// 64 x 32 (B) are staged in the no-swizzle K-major core-matrix layout (core
+// matrices of 8 rows x 16 bytes, 128 bytes apart along k, 1024 bytes apart
+// between 8-row groups), made visible to the tensor cores by a proxy fence,
+// and one thread issues the MMAs and commits them to the mbarrier, on which
+// every thread waits with a bounded poll (on time-out the CTA's status
+// becomes STN_ETIMEOUT and the product is abandoned).
+struct TcState {
+  uint64_t bar;    // mbarrier the MMAs of a stage complete on
+  uint32_t tmem;   // tensor-memory address of the accumulator
+  uint32_t phase;  // parity of the barrier's next completion
+  int enabled;     // the kernel allocated tensor memory and staging space
+  int failed;      // a bounded wait ran out
+  float *stage;    // 6 x 128 x 32 + 4 x 64 x 32 floats of shared memory
+};
+static __shared__ __align__(8) TcState g_tc;
+
+constexpr int kTcM = 128, kTcN = 64, kTcK = 32;
+constexpr int kTcStageFloats = 6 * kTcM * kTcK + 4 * kTcN * kTcK;
+constexpr uint32_t kTcCols = 2 * kTcN;
+constexpr long long kTcWaitLimit = 1ll << 24;
+// kind::tf32, FP32 accumulator, both operands K-major, N = 64, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(kTcN >> 3) << 17) |
+                              (static_cast<uint32_t>(kTcM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Float index of element (row, k) of a row x 32 tile in the core-matrix layout.
+__device__ __forceinline__ int tc_index(int row, int k) {
+  return (((row >> 3) * (kTcK / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4) >> 2;
+}
+
+// Descriptor of the 8-wide k slice q of a staged tile (version 1, no swizzle).
+__device__ __forceinline__ uint64_t tc_desc(const float *tile, int q) {
+  const uint32_t a = smem_u32(tile) + static_cast<uint32_t>(q) * 256u;
+  return static_cast<uint64_t>((a >> 4) & 0x3FFF) | (static_cast<uint64_t>(128 >> 4) << 16) |
+         (static_cast<uint64_t>((kTcK / 4 * 128) >> 4) << 32) | (static_cast<uint64_t>(1) << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+      :
+      : "r"(d), "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t phase) {
+  for (long long it = 0; it < kTcWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Tensor memory and barrier of a CTA that runs tensor-core GEMMs (CTA-wide;
+// warp 0 allocates).  stage: kTcStageFloats floats of shared memory, free
+// whenever a GEMM runs.
+static __device__ void tc_setup(float *stage) {
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&g_tc.tmem)),
+                 "r"(kTcCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&g_tc.bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    g_tc.phase = 0;
+    g_tc.failed = 0;
+    g_tc.stage = stage;
+    g_tc.enabled = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+}
+
+static __device__ void tc_teardown() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(g_tc.tmem), "r"(kTcCols));
+}
+
+static __device__ __forceinline__ void tc_disable() {
+  if (threadIdx.x == 0) g_tc.enabled = 0;
+  __syncthreads();
+}
+
+static_assert(kThreads == 512, "the tensor-core epilogue maps 16 warps onto 4 lane quarters x 4 column blocks");
+
+template <int TA, int TB>
+static __device__ void cgemm_tc(int M, int N, int K, cplx<float> alpha, const cplx<float> *A, int lda,
+                                const cplx<float> *B, int ldb, cplx<float> beta, cplx<float> *C, int ldc) {
+  float *st = g_tc.stage;
+  float *arh = st, *arl = st + kTcM * kTcK, *aih = st + 2 * kTcM * kTcK, *ail = st + 3 * kTcM * kTcK;
+  float *nih = st + 4 * kTcM * kTcK, *nil = st + 5 * kTcM * kTcK;
+  float *brh = st + 6 * kTcM * kTcK, *brl = brh + kTcN * kTcK, *bih = brl + kTcN * kTcK, *bil = bih + kTcN * kTcK;
+  const uint32_t tm_re = g_tc.tmem, tm_im = g_tc.tmem + kTcN;
+  const uint32_t bar = smem_u32(&g_tc.bar);
+  uint32_t phase = g_tc.phase;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool beta0 = beta.re == 0.f && beta.im == 0.f;
+  bool ok = true;
+  for (int i0 = 0; i0 < M && ok; i0 += kTcM) {
+    for (int j0 = 0; j0 < N && ok; j0 += kTcN) {
+      for (int k0 = 0; k0 < K; k0 += kTcK) {
+        for (int e = threadIdx.x; e < kTcM * kTcK; e += kThreads) {
+          int i, k;
+          if (TA == 0) { k = e % kTcK; i = e / kTcK; } else { i = e % kTcM; k = e / kTcM; }
+          const int gi = i0 + i, gk = k0 + k;
+          cplx<float> v = cmake<float>(0.f, 0.f);
+          if (gi < M && gk < K)
+            v = TA == 0 ? A[static_cast<int64_t>(gi) * lda + gk] : cconj(A[static_cast<int64_t>(gk) * lda + gi]);
+          const int o = tc_index(i, k);
+          const float rh = tf32_round(v.re), ih = tf32_round(v.im);
+          const float rl = tf32_round(v.re - rh), il = tf32_round(v.im - ih);
+          arh[o] = rh; arl[o] = rl; aih[o] = ih; ail[o] = il; nih[o] = -ih; nil[o] = -il;
+        }
+        for (int e = threadIdx.x; e < kTcN * kTcK; e += kThreads) {
+          int j, k;
+          if (TB == 0) { j = e % kTcN; k = e / kTcN; } else { k = e % kTcK; j = e / kTcK; }
+          const int gj = j0 + j, gk = k0 + k;
+          cplx<float> v = cmake<float>(0.f, 0.f);
+          if (gj < N && gk < K)
+            v = TB == 0 ? B[static_cast<int64_t>(gk) * ldb + gj] : cconj(B[static_cast<int64_t>(gj) * ldb + gk]);
+          const int o = tc_index(j, k);
+          const float rh = tf32_round(v.re), ih = tf32_round(v.im);
+          brh[o] = rh; brl[o] = tf32_round(v.re - rh); bih[o] = ih; bil[o] = tf32_round(v.im - ih);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        if (threadIdx.x == 0) {
+#pragma unroll
+          for (int q = 0; q < kTcK / 8; ++q) {
+            const uint32_t acc = (k0 > 0 || q > 0) ? 1u : 0u;
+            const uint64_t a_rh = tc_desc(arh, q), a_rl = tc_desc(arl, q), a_ih = tc_desc(aih, q),
+                           a_il = tc_desc(ail, q), a_nh = tc_desc(nih, q), a_nl = tc_desc(nil, q);
+            const uint64_t b_rh = tc_desc(brh, q), b_rl = tc_desc(brl, q), b_ih = tc_desc(bih, q),
+                           b_il = tc_desc(bil, q);
+            tc_mma(tm_re, a_rh, b_rh, acc);  // Re A Re B
+            tc_mma(tm_re, a_rh, b_rl, 1u);
+            tc_mma(tm_re, a_rl, b_rh, 1u);
+            tc_mma(tm_re, a_nh, b_ih, 1u);   // - Im A Im B
+            tc_mma(tm_re, a_nh, b_il, 1u);
+            tc_mma(tm_re, a_nl, b_ih, 1u);
+            tc_mma(tm_im, a_rh, b_ih, acc);  // Re A Im B
+            tc_mma(tm_im, a_rh, b_il, 1u);
+            tc_mma(tm_im, a_rl, b_ih, 1u);
+            tc_mma(tm_im, a_ih, b_rh, 1u);   // Im A Re B
+            tc_mma(tm_im, a_ih, b_rl, 1u);
+            tc_mma(tm_im, a_il, b_rh, 1u);
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                       : "memory");
+        }
+        if (!tc_wait(bar, phase) && lane == 0) atomicExch(&g_tc.failed, 1);
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        __syncthreads();
+        if (g_tc.failed) {
+          ok = false;
+          break;
+        }
+      }
+      if (!ok) break;
+      // epilogue: warp w reads lanes 32 (w % 4) .. + 31, columns 16 (w / 4) .. + 15,
+      // eight at a time
+      const int quarter = warp & 3;
+      const uint32_t lane_off = static_cast<uint32_t>(32 * quarter) << 16;
+      const int row = i0 + 32 * quarter + lane;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int cb = 16 * (warp >> 2) + 8 * half;
+        uint32_t vr[8], vi[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                     : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]),
+                       "=r"(vr[7])
+                     : "r"(tm_re + lane_off + cb));
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                     : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]),
+                       "=r"(vi[7])
+                     : "r"(tm_im + lane_off + cb));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (row < M) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const int col = j0 + cb + c;
+            if (col >= N) continue;
+            cplx<float> v = cmul(alpha, cmake<float>(__uint_as_float(vr[c]), __uint_as_float(vi[c])));
+            cplx<float> *dst = &C[static_cast<int64_t>(row) * ldc + col];
+            if (!beta0) v = cadd(v, cmul(beta, *dst));
+            *dst = v;
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+    }
+  }
+  if (threadIdx.x == 0) g_tc.phase = phase;
+  __syncthreads();
+}
+
 // C = alpha * op(A) op(B) + beta * C, all row-major, op = identity (0) or
-// conjugate transpose (1).  op(A) is M x K, op(B) is K x N.
+// conjugate transpose (1).  op(A) is M x K, op(B) is K x N.  Complex64
+// products large enough to fill the tensor-core tiles run cgemm_tc when the
+// kernel enabled it; the rest (and complex128) run on the CUDA cores below.
 template <typename T, int TA, int TB>
 static __device__ void cgemm(int M, int N, int K, cplx<T> alpha, const cplx<T> *A, int lda,
                       const cplx<T> *B, int ldb, cplx<T> beta, cplx<T> *C, int ldc,
                       cplx<T> *tile) {
+  if constexpr (sizeof(T) == 4) {
+    if (g_tc.enabled && M >= 64 && N >= 32 && K >= 32) {
+      cgemm_tc<TA, TB>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+      return;
+    }
+  }
   // thread (ty, tx) of a kTY x 16 grid owns rows ty + kTY a (a < kMR) and
   // columns tx + 16 b (b < 4) of the 64 x 64 output tile
   constexpr int kTY = kThreads / 16, kMR = kBM / kTY;
@@ -1928,6 +2172,12 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
   const int n = P.n, W = P.W;
   Smem<T> S = carve<T>(smem_raw, n, W, P.svd_elems);
   Scratch<T> X = scratch_for<T>(P, P.work_c);
+  // complex64: the large contractions run on the tensor cores, staged in the
+  // shared SVD buffer (free whenever a GEMM runs)
+  bool tc_alloc = false;
+  if constexpr (sizeof(T) == 4) tc_alloc = P.use_tc && static_cast<int64_t>(P.svd_elems) * 2 >= kTcStageFloats;
+  if (tc_alloc) tc_setup(reinterpret_cast<float *>(S.jbuf));
+  else tc_disable();
   // With a ticket counter the CTAs take the batch's shots in order as they
   // finish (a work queue that balances uneven shots when the batch holds
   // more shots than CTAs); without one, shots are grid-strided.
@@ -1960,6 +2210,14 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
     long long t_ops = clock64();
     const uint64_t gshot = (P.shot_offset_dev ? *P.shot_offset_dev : P.shot_offset) + static_cast<uint64_t>(shot);
     for (int oi = P.op_begin; oi < P.op_end; ++oi) {
+      if (g_tc.failed) {  // a tensor-core wait ran out: this shot stops, the rest use the CUDA cores
+        if (tid() == 0) {
+          S.misc[M_FAIL] = STN_ETIMEOUT;
+          g_tc.failed = 0;
+          g_tc.enabled = 0;
+        }
+        __syncthreads();
+      }
       if (S.misc[M_FAIL]) break;
       const Op op = P.ops[oi];
       switch (op.kind) {
@@ -2165,6 +2423,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
     }
     __syncthreads();
   }
+  if (tc_alloc) tc_teardown();
 }
 
 // Identity frame, |0...0>, cleared records and accumulators.
@@ -2206,6 +2465,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 1) dense_check_kernel(int what, int m, int n, cplx<T> *A,
                                                                   cplx<T> *V, T *sig2, int use_smem) {
   extern __shared__ __align__(16) char smem_raw[];
+  tc_disable();
   double *red = reinterpret_cast<double *>(smem_raw);
   double *dm = red + kThreads;
   int *flag = reinterpret_cast<int *>(dm + 16);
@@ -2300,6 +2560,7 @@ __global__ void __launch_bounds__(kThreads, 1) diag_kernel(EngineParams P, int w
                                                            const int32_t *lq, int nl, int letter, double *out,
                                                            int *count) {
   extern __shared__ __align__(16) char smem_raw[];
+  tc_disable();
   const int n = P.n, W = P.W;
   Smem<T> S = carve<T>(smem_raw, n, W, P.svd_elems);
   Scratch<T> X = scratch_for<T>(P, P.work_c);
@@ -2449,6 +2710,7 @@ static __device__ cplx<double> mps_overlap(const EngineParams &P, const Smem<T> 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(EngineParams P, double *grad) {
   extern __shared__ __align__(16) char smem_raw[];
+  tc_disable();
   const int n = P.n, W = P.W;
   Smem<T> S = carve<T>(smem_raw, n, W, P.svd_elems);
   Scratch<T> X = scratch_for<T>(P, P.work_c);

@@ -23,6 +23,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 1) svd_noalloc_kernel(int m, int n, const cplx<T> *C,
                                                                   cplx<T> *work, cplx<T> *V, T *sig2) {
   extern __shared__ __align__(16) char smem_raw[];
+  tc_disable();
   double *red = reinterpret_cast<double *>(smem_raw);
   double *dm = red + kThreads;
   int *flag = reinterpret_cast<int *>(dm + 16);
