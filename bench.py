@@ -64,6 +64,9 @@ def parse(argv=None):
     ap.add_argument("--precision", default="c64", choices=["c64", "c128", "c64-svd64"],
                     help="c128: the plain per-shot complex128 GPU path on the same workload (comparator); "
                          "c64-svd64: complex64 contractions with every bond SVD in FP64")
+    ap.add_argument("--gemm", default="tensor", choices=["tensor", "fma"],
+                    help="complex64 contraction units: tcgen05 tensor cores (TF32 3-term split, FP32 "
+                         "accumulation) or the CUDA cores")
     ap.add_argument("--dense-routines", action="store_true",
                     help="time the truncation sweep's dense routines alone on one CTA and exit")
     return ap.parse_args(argv)
@@ -371,7 +374,8 @@ def main():
     B = args.shots if args.shots > 0 else sms
     stream = torch.cuda.current_stream()
     peaks = measure_peaks(stn, torch, stream)
-    sim = stn.Simulator(w, max_shots=B, stream=stream.cuda_stream)
+    gemm_units = stn.GEMM_TENSOR if args.gemm == "tensor" else stn.GEMM_FMA
+    sim = stn.Simulator(w, max_shots=B, stream=stream.cuda_stream, gemm_units=gemm_units)
     theta = theta_table(w, sim.n_pairs)
     th_host = torch.tensor(theta, dtype=torch.float64).pin_memory()
     d_theta = torch.empty_like(th_host, device="cuda")
@@ -482,6 +486,8 @@ def main():
                 "vs_baseline": None, "dtype": {0: "c128", 1: "c64", 2: "c64+f64svd"}[w.precision], "data": "synthetic",
                 "config": {"workload": w.name, "distance": w.distance, "rounds": w.rounds, "theta": w.theta,
                            "p": w.p, "chi_cap": w.chi_cap, "shots_per_batch_per_rank": B,
+                           "contractions": ("tcgen05 tensor cores, TF32 3-term split, FP32 accumulation"
+                                            if args.gemm == "tensor" and w.precision else "CUDA cores"),
                            "step": "one layer step over the batch: CNOT layer l of round r with its crosstalk "
                                    "rotations (the round's H gates and ancilla measurements in its first and last "
                                    "layer, the final readout in the last step); 4 x 5 = 20 steps = one batch",

@@ -61,6 +61,7 @@ enum { STN_PAIRS_ADJACENT_IDLE = 0, STN_PAIRS_ADJACENT_IDLE_DIAG_XX = 1 };
 enum { STN_PRECISION_C128 = 0, STN_PRECISION_C64 = 1, STN_PRECISION_C64_SVD64 = 2 };
 enum { STN_BASIS_Z = 0, STN_BASIS_X = 1 };
 enum { STN_LAYERS_IDLE = 0xFF }; /* pair_layer_mask entry: use the idle rule */
+enum { STN_GEMM_TENSOR = 0, STN_GEMM_FMA = 1 }; /* stn_config.gemm_units */
 
 /* Simulation parameters: the problem statement of Sec. II-III (code
  * distance, rounds, CNOT schedule, crosstalk pairs and angles, Pauli noise
@@ -110,6 +111,12 @@ typedef struct {
                             this many bytes, and a sweep that needs more stops
                             its shot with STN_EOVERFLOW (reported by the next
                             synchronising call) */
+  int32_t gemm_units;      /* STN_GEMM_TENSOR (0): complex64 contractions of at
+                            least 64 x 32 x 16 run on the tcgen05 tensor cores
+                            (TF32 operands split into head and tail, FP32
+                            accumulation: FP32-accurate products);
+                            STN_GEMM_FMA (1): every contraction on the CUDA
+                            cores.  Complex128 always uses the CUDA cores */
 } stn_config;
 
 /* Per-shot diagnostics of the last batch (Sec. IV B: truncation). */
@@ -397,6 +404,27 @@ stn_status stn_dense_svd_noalloc(int32_t precision, int32_t m, int32_t n, const 
  * failure. */
 stn_status stn_dense_gemm_tc(int32_t m, int32_t n, int32_t k, const float *d_a, const float *d_b, float *d_c,
                              int32_t *d_status, void *cuda_stream);
+
+/* The complex contraction of the MPS sweeps (R_k A'_k, C = R_k M_k,
+ * M_k V_keep, A'_{k-1} W, the transfer products; Sec. IV A-B) alone on one
+ * CTA, through the same device routine the round kernel calls:
+ *   C = alpha op(A) op(B) + beta C
+ * row-major complex of the precision (0: complex128, 1: complex64; device
+ * memory), op = identity (0) or conjugate transpose (1), op(A) m x k, op(B)
+ * k x n, lda / ldb / ldc the row strides of A, B, C as stored (lda >= k for
+ * op_a = 0, >= m for op_a = 1; likewise ldb; ldc >= n); each of m, n, k in
+ * 1..4096.  alpha and beta: host (re, im) pairs, rounded to the precision.
+ * gemm_units as in stn_config: STN_GEMM_TENSOR runs complex64 products of at
+ * least 64 x 32 x 16 on the tcgen05 tensor cores (TF32 3-term split, FP32
+ * accumulation), STN_GEMM_FMA (and complex128) on the CUDA cores.
+ * *d_status (device int, caller-zeroed) becomes STN_ETIMEOUT if a bounded
+ * wait for the tensor cores ran out.  Asynchronous on cuda_stream.
+ * Errors: STN_EINVAL on bad sizes, strides, ops or null pointers, STN_ECUDA
+ * on launch failure. */
+stn_status stn_dense_cgemm(int32_t precision, int32_t gemm_units, int32_t op_a, int32_t op_b, int32_t m,
+                           int32_t n, int32_t k, const double *alpha, const void *d_a, int32_t lda,
+                           const void *d_b, int32_t ldb, const double *beta, void *d_c, int32_t ldc,
+                           int32_t *d_status, void *cuda_stream);
 
 /* Arithmetic-peak probe (the paper has no counterpart: it measures the
  * denominators of the roofline the kernels are placed on).  Launches on

@@ -14,6 +14,7 @@ import numpy as np
 from ._native import Config, ShotStats, build, load
 
 STN_OK, STN_EINVAL, STN_ENOMEM, STN_ECUDA, STN_ETIMEOUT, STN_ENUMERIC, STN_ENOTIMPL, STN_EOVERFLOW = range(8)
+GEMM_TENSOR, GEMM_FMA = 0, 1  # stn_config.gemm_units
 PAIR_RULES = {"adjacent_idle": 0, "adjacent_idle+diag_xx": 1}
 OP_KINDS = {1: "RN", 2: "H", 3: "D1", 4: "CX", 5: "D2", 6: "ROT", 7: "M"}
 
@@ -74,13 +75,15 @@ def layout(distance):
 
 class Simulator:
     """One stn_ctx: a compiled program plus device state for max_shots shots.
-    arena_cap_bytes > 0 caps each resident shot's stack of span tensors (see
-    stn_config)."""
+    arena_cap_bytes > 0 caps each resident shot's stack of span tensors;
+    gemm_units picks the complex64 contraction units (GEMM_TENSOR: tcgen05
+    tensor cores, GEMM_FMA: CUDA cores; see stn_config)."""
 
-    def __init__(self, workload, max_shots, stream=0, arena_cap_bytes=0):
+    def __init__(self, workload, max_shots, stream=0, arena_cap_bytes=0, gemm_units=GEMM_TENSOR):
         self.lib = load()
         self.cfg = config_from_workload(workload)
         self.cfg.arena_cap_bytes = int(arena_cap_bytes)
+        self.cfg.gemm_units = int(gemm_units)
         ctx = ctypes.c_void_p()
         st = self.lib.stn_create(ctypes.byref(self.cfg), int(max_shots), ctypes.c_void_p(stream),
                                  ctypes.byref(ctx))
@@ -314,6 +317,20 @@ def dense_gemm_tc(m, n, k, d_a, d_b, d_c, d_status, stream=0):
                                   ctypes.c_void_p(d_c), ctypes.c_void_p(d_status), ctypes.c_void_p(stream))
     if st != STN_OK:
         raise StnError(st, "stn_dense_gemm_tc failed")
+
+
+def dense_cgemm(precision, op_a, op_b, m, n, k, d_a, lda, d_b, ldb, d_c, ldc, d_status, alpha=1.0, beta=0.0,
+                gemm_units=GEMM_TENSOR, stream=0):
+    """stn_dense_cgemm: d_c = alpha op(A) op(B) + beta d_c (row-major complex
+    device buffers, op 0 = identity, 1 = conjugate transpose) on one CTA
+    through the sweeps' contraction routine."""
+    al = (ctypes.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+    be = (ctypes.c_double * 2)(complex(beta).real, complex(beta).imag)
+    st = load().stn_dense_cgemm(int(precision), int(gemm_units), int(op_a), int(op_b), int(m), int(n), int(k),
+                                al, ctypes.c_void_p(d_a), int(lda), ctypes.c_void_p(d_b), int(ldb), be,
+                                ctypes.c_void_p(d_c), int(ldc), ctypes.c_void_p(d_status), ctypes.c_void_p(stream))
+    if st != STN_OK:
+        raise StnError(st, "stn_dense_cgemm failed")
 
 
 def peak_probe(kind, iters, stream=0):

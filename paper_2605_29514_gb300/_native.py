@@ -72,6 +72,7 @@ class Config(ctypes.Structure):
         ("pair_pauli", ctypes.c_void_p),
         ("pair_layer_mask", ctypes.c_void_p),
         ("arena_cap_bytes", ctypes.c_int64),
+        ("gemm_units", ctypes.c_int32),
     ]
 
 
@@ -138,6 +139,11 @@ EXPORTS = [
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("stn_dense_gemm_tc", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("stn_dense_cgemm", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     ("stn_peak_probe", ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                       ctypes.c_void_p]),
     ("stn_philox_uniforms", ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,

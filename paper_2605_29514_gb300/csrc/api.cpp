@@ -120,7 +120,7 @@ stn::EngineParams params(const stn_ctx *c, int op_begin, int op_end, const doubl
   p.work_c = c->plan.work_c;
   p.svd_elems = c->svd_elems;
   p.svd64_all = c->cfg.precision == STN_PRECISION_C64_SVD64 ? 1 : 0;
-  p.use_tc = c->cfg.precision != STN_PRECISION_C128 ? 1 : 0;
+  p.use_tc = c->cfg.precision != STN_PRECISION_C128 && c->cfg.gemm_units == STN_GEMM_TENSOR ? 1 : 0;
   p.err = c->d_err;
   return p;
 }
@@ -147,6 +147,8 @@ std::string validate(const stn_config *cfg) {
   if (cfg->n_pairs < 0 || cfg->n_pairs > 4096) return "n_pairs must be 0..4096";
   if (cfg->n_pairs > 0 && !cfg->pairs) return "pairs is NULL with n_pairs > 0";
   if (cfg->arena_cap_bytes < 0) return "arena_cap_bytes must be >= 0";
+  if (cfg->gemm_units != STN_GEMM_TENSOR && cfg->gemm_units != STN_GEMM_FMA)
+    return "gemm_units must be STN_GEMM_TENSOR or STN_GEMM_FMA";
   return std::string();
 }
 
@@ -806,6 +808,26 @@ stn_status stn_dense_svd(int32_t precision, int32_t m, int32_t n, void *d_c, voi
   if (in_shared == 3 && (m > 1024 || 2 * n + 4 > stn::svd_smem_elems(precision))) return STN_EINVAL;
   cudaError_t e = stn::launch_dense_check(precision, 1, m, n, d_c, d_v, d_sig2, in_shared,
                                           static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? STN_OK : STN_ECUDA;
+}
+
+stn_status stn_dense_cgemm(int32_t precision, int32_t gemm_units, int32_t op_a, int32_t op_b, int32_t m,
+                           int32_t n, int32_t k, const double *alpha, const void *d_a, int32_t lda,
+                           const void *d_b, int32_t ldb, const double *beta, void *d_c, int32_t ldc,
+                           int32_t *d_status, void *cuda_stream) {
+  if ((precision != 0 && precision != 1) || (gemm_units != STN_GEMM_TENSOR && gemm_units != STN_GEMM_FMA) ||
+      (op_a != 0 && op_a != 1) || (op_b != 0 && op_b != 1))
+    return STN_EINVAL;
+  if (m < 1 || n < 1 || k < 1 || m > 4096 || n > 4096 || k > 4096) return STN_EINVAL;
+  if (lda < (op_a ? m : k) || ldb < (op_b ? k : n) || ldc < n) return STN_EINVAL;
+  if (!alpha || !beta || !d_a || !d_b || !d_c || !d_status) return STN_EINVAL;
+  const int use_tc = precision == 1 && gemm_units == STN_GEMM_TENSOR ? 1 : 0;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = precision == 0
+                      ? stn::launch_dense_gemm_f64(op_a, op_b, m, n, k, alpha, d_a, lda, d_b, ldb, beta, d_c, ldc,
+                                                   use_tc, d_status, s)
+                      : stn::launch_dense_gemm_f32(op_a, op_b, m, n, k, alpha, d_a, lda, d_b, ldb, beta, d_c, ldc,
+                                                   use_tc, d_status, s);
   return e == cudaSuccess ? STN_OK : STN_ECUDA;
 }
 

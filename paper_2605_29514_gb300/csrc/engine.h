@@ -106,6 +106,14 @@ cudaError_t launch_diag_f64(const EngineParams &p, int what, int target, int cut
                             int letter, double *out, int *count, int grid, cudaStream_t s);
 cudaError_t launch_dense_check(int precision, int what, int m, int n, void *A, void *V, void *sig2,
                                int use_smem, cudaStream_t s);
+// C = alpha op(A) op(B) + beta C on one CTA through the sweeps' cgemm
+// (alpha, beta: host re/im pairs); use_tc: complex64 on the tensor cores
+cudaError_t launch_dense_gemm_f32(int ta, int tb, int m, int n, int k, const double *alpha, const void *A, int lda,
+                                  const void *B, int ldb, const double *beta, void *C, int ldc, int use_tc,
+                                  int *status, cudaStream_t s);
+cudaError_t launch_dense_gemm_f64(int ta, int tb, int m, int n, int k, const double *alpha, const void *A, int lda,
+                                  const void *B, int ldb, const double *beta, void *C, int ldc, int use_tc,
+                                  int *status, cudaStream_t s);
 int svd_smem_elems(int precision);
 size_t noalloc_scratch_bytes();
 cudaError_t launch_svd_noalloc(int precision, int m, int n, const void *C, void *V, void *sig2,

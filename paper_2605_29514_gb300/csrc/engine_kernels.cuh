@@ -160,34 +160,42 @@ static __device__ double block_sum(double v, double *red) {
 // ---------------------------------------------------------------------------
 // Complex64 GEMM on the fifth-generation tensor cores (tcgen05).  The CTA's
 // tensor-memory accumulator (128 lanes x 128 FP32 columns: the real part of
-// a 128 x 64 output tile, then its imaginary part), the mbarrier the MMAs
-// complete on and the shared-memory staging area of the operand tiles live
-// in g_tc; a kernel that allocates the accumulator sets enabled.
+// a 128 x 64 output tile, then its imaginary part), the two mbarriers the
+// MMAs complete on and the shared-memory staging area of the operand tiles
+// live in g_tc; a kernel that allocates the accumulator sets enabled.
 //
 // Each product is FP32-accurate from TF32 operands by the 3-term split
 // (Ootomo and Yokota, 2022): x = x_hi + x_lo with both parts TF32, and
 // A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi.  The complex product takes four
-// real ones: Re C = Re A Re B - Im A Im B, Im C = Re A Im B + Im A Re B, so
-// every k step of 8 issues 12 MMAs per part (M = 128, N = 64, K = 8,
-// kind::tf32), accumulated in FP32.  Operand tiles of 128 x 32 (A) and
-// 64 x 32 (B) are staged in the no-swizzle K-major core-matrix layout (core
-// matrices of 8 rows x 16 bytes, 128 bytes apart along k, 1024 bytes apart
-// between 8-row groups), made visible to the tensor cores by a proxy fence,
-// and one thread issues the MMAs and commits them to the mbarrier, on which
-// every thread waits with a bounded poll (on time-out the CTA's status
-// becomes STN_ETIMEOUT and the product is abandoned).
+// real ones, Re C = Re A Re B + Im A (-Im B) and Im C = Re A Im B + Im A Re B,
+// so every k step of 8 issues 6 MMAs per part (M = 128, N = 64, K = 8,
+// kind::tf32) accumulated in FP32; the negated imaginary part is staged on
+// the smaller B tile.  The k range goes in chunks of 16: the 128 x 16 A tile
+// (4 arrays: Re and Im, head and tail) and the 64 x 16 B tile (6 arrays:
+// Re, Im and -Im, head and tail) of a chunk are written to one of two
+// staging buffers in the no-swizzle K-major core-matrix layout (core
+// matrices of 8 rows x 16 bytes, 128 bytes apart along k, 512 bytes apart
+// between 8-row groups), each thread storing whole 16-byte core-matrix rows
+// so that a quarter warp fills one core matrix without bank conflicts.  After
+// a proxy fence one thread issues the chunk's 24 MMAs and commits them to the
+// buffer's mbarrier, and the CTA stages the next chunk into the other buffer
+// while they run; a buffer is refilled only after a bounded wait on its
+// barrier (on time-out the CTA's status becomes STN_ETIMEOUT and the product
+// is abandoned).
 struct TcState {
-  uint64_t bar;    // mbarrier the MMAs of a stage complete on
-  uint32_t tmem;   // tensor-memory address of the accumulator
-  uint32_t phase;  // parity of the barrier's next completion
-  int enabled;     // the kernel allocated tensor memory and staging space
-  int failed;      // a bounded wait ran out
-  float *stage;    // 6 x 128 x 32 + 4 x 64 x 32 floats of shared memory
+  uint64_t bar[2];  // mbarriers of the two staging buffers
+  uint32_t tmem;    // tensor-memory address of the accumulator
+  uint32_t phase;   // bit b: parity of bar[b]'s next completion
+  int enabled;      // the kernel allocated tensor memory and staging space
+  int failed;       // a bounded wait ran out
+  float *stage;     // two staging buffers of kTcBufFloats floats
 };
 static __shared__ __align__(8) TcState g_tc;
 
-constexpr int kTcM = 128, kTcN = 64, kTcK = 32;
-constexpr int kTcStageFloats = 6 * kTcM * kTcK + 4 * kTcN * kTcK;
+constexpr int kTcM = 128, kTcN = 64, kTcK = 16;
+constexpr int kTcAFloats = kTcM * kTcK, kTcBFloats = kTcN * kTcK;
+constexpr int kTcBufFloats = 4 * kTcAFloats + 6 * kTcBFloats;
+constexpr int kTcStageFloats = 2 * kTcBufFloats;
 constexpr uint32_t kTcCols = 2 * kTcN;
 constexpr long long kTcWaitLimit = 1ll << 24;
 // kind::tf32, FP32 accumulator, both operands K-major, N = 64, M = 128
@@ -198,18 +206,23 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// TF32 rounding (round to nearest, ties away) of an FP32 value, returned as
+// the FP32 number it represents.
 __device__ __forceinline__ float tf32_round(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
 
-// Float index of element (row, k) of a row x 32 tile in the core-matrix layout.
-__device__ __forceinline__ int tc_index(int row, int k) {
-  return (((row >> 3) * (kTcK / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4) >> 2;
+// Float offset of the 16-byte core-matrix row (row, k = 4 kg .. 4 kg + 3)
+// of a row x kTcK tile.
+__device__ __forceinline__ int tc_row_offset(int row, int kg) {
+  return (((row >> 3) * (kTcK / 4) + kg) * 128 + (row & 7) * 16) >> 2;
 }
 
-// Descriptor of the 8-wide k slice q of a staged tile (version 1, no swizzle).
+// Descriptor of the 8-wide k slice q of a staged tile (version 1, no
+// swizzle): leading byte offset 128 (the next core matrix along k), stride
+// byte offset kTcK / 4 x 128 (the next 8-row group).
 __device__ __forceinline__ uint64_t tc_desc(const float *tile, int q) {
   const uint32_t a = smem_u32(tile) + static_cast<uint32_t>(q) * 256u;
   return static_cast<uint64_t>((a >> 4) & 0x3FFF) | (static_cast<uint64_t>(128 >> 4) << 16) |
@@ -240,9 +253,9 @@ __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t phase) {
   return false;
 }
 
-// Tensor memory and barrier of a CTA that runs tensor-core GEMMs (CTA-wide;
-// warp 0 allocates).  stage: kTcStageFloats floats of shared memory, free
-// whenever a GEMM runs.
+// Tensor memory and barriers of a CTA that runs tensor-core GEMMs (CTA-wide;
+// warp 0 allocates).  stage: kTcStageFloats floats of shared memory, 16-byte
+// aligned, free whenever a GEMM runs.
 static __device__ void tc_setup(float *stage) {
   if ((threadIdx.x >> 5) == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&g_tc.tmem)),
@@ -250,7 +263,8 @@ static __device__ void tc_setup(float *stage) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&g_tc.bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&g_tc.bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&g_tc.bar[1])));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     g_tc.phase = 0;
     g_tc.failed = 0;
@@ -275,85 +289,141 @@ static __device__ __forceinline__ void tc_disable() {
   __syncthreads();
 }
 
-static_assert(kThreads == 512, "the tensor-core epilogue maps 16 warps onto 4 lane quarters x 4 column blocks");
+static_assert(kThreads == 512, "the tensor-core staging and epilogue map 512 threads onto the tiles");
 
+__device__ __forceinline__ void st_f4(float *p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+
+// Stages the k chunk k0 .. k0 + kTcK - 1 of rows i0 .. i0 + 127 of op(A) and
+// columns j0 .. j0 + 63 of op(B) into the staging buffer buf (zero outside
+// the matrices).  Item f of a tile is the core-matrix row (row, kg) with
+// row = (f & 7) + 8 (f >> 5) and kg = (f >> 3) & 3, so that the eight
+// threads of a quarter warp write the eight rows of one core matrix.
 template <int TA, int TB>
-static __device__ void cgemm_tc(int M, int N, int K, cplx<float> alpha, const cplx<float> *A, int lda,
-                                const cplx<float> *B, int ldb, cplx<float> beta, cplx<float> *C, int ldc) {
+static __device__ __forceinline__ void tc_stage(float *buf, int M, int N, int K, const cplx<float> *A, int lda,
+                                                const cplx<float> *B, int ldb, int i0, int j0, int k0) {
+  for (int e = threadIdx.x; e < 4 * (kTcM + kTcN); e += kThreads) {
+    const bool isA = e < 4 * kTcM;  // warp-uniform: 4 kTcM is a multiple of kThreads
+    const int f = isA ? e : e - 4 * kTcM;
+    const int row = (f & 7) | ((f >> 5) << 3), kg = (f >> 3) & 3;
+    float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int gk = k0 + 4 * kg + u;
+      cplx<float> v = cmake<float>(0.f, 0.f);
+      if (isA) {
+        const int gi = i0 + row;
+        if (gi < M && gk < K)
+          v = TA == 0 ? A[static_cast<int64_t>(gi) * lda + gk] : cconj(A[static_cast<int64_t>(gk) * lda + gi]);
+      } else {
+        const int gj = j0 + row;
+        if (gj < N && gk < K)
+          v = TB == 0 ? B[static_cast<int64_t>(gk) * ldb + gj] : cconj(B[static_cast<int64_t>(gj) * ldb + gk]);
+      }
+      rh[u] = tf32_round(v.re);
+      rl[u] = tf32_round(v.re - rh[u]);
+      ih[u] = tf32_round(v.im);
+      il[u] = tf32_round(v.im - ih[u]);
+    }
+    const int o = tc_row_offset(row, kg);
+    float *dst = isA ? buf + o : buf + 4 * kTcAFloats + o;
+    const int s = isA ? kTcAFloats : kTcBFloats;
+    st_f4(dst, rh[0], rh[1], rh[2], rh[3]);
+    st_f4(dst + s, rl[0], rl[1], rl[2], rl[3]);
+    st_f4(dst + 2 * s, ih[0], ih[1], ih[2], ih[3]);
+    st_f4(dst + 3 * s, il[0], il[1], il[2], il[3]);
+    if (!isA) {
+      st_f4(dst + 4 * s, -ih[0], -ih[1], -ih[2], -ih[3]);
+      st_f4(dst + 5 * s, -il[0], -il[1], -il[2], -il[3]);
+    }
+  }
+}
+
+// The 24 MMAs of one staged chunk (two k slices of 8) into the real and
+// imaginary accumulators; the first slice of a tile overwrites them.
+static __device__ __forceinline__ void tc_issue_chunk(const float *buf, uint32_t tm_re, uint32_t tm_im, bool first) {
+  const float *Ab = buf, *Bb = buf + 4 * kTcAFloats;
+#pragma unroll
+  for (int q = 0; q < kTcK / 8; ++q) {
+    const uint32_t acc = (!first || q > 0) ? 1u : 0u;
+    const uint64_t a_rh = tc_desc(Ab, q), a_rl = tc_desc(Ab + kTcAFloats, q), a_ih = tc_desc(Ab + 2 * kTcAFloats, q),
+                   a_il = tc_desc(Ab + 3 * kTcAFloats, q);
+    const uint64_t b_rh = tc_desc(Bb, q), b_rl = tc_desc(Bb + kTcBFloats, q), b_ih = tc_desc(Bb + 2 * kTcBFloats, q),
+                   b_il = tc_desc(Bb + 3 * kTcBFloats, q), b_nh = tc_desc(Bb + 4 * kTcBFloats, q),
+                   b_nl = tc_desc(Bb + 5 * kTcBFloats, q);
+    tc_mma(tm_re, a_rh, b_rh, acc);  // Re A Re B
+    tc_mma(tm_re, a_rh, b_rl, 1u);
+    tc_mma(tm_re, a_rl, b_rh, 1u);
+    tc_mma(tm_re, a_ih, b_nh, 1u);   // Im A (-Im B)
+    tc_mma(tm_re, a_ih, b_nl, 1u);
+    tc_mma(tm_re, a_il, b_nh, 1u);
+    tc_mma(tm_im, a_rh, b_ih, acc);  // Re A Im B
+    tc_mma(tm_im, a_rh, b_il, 1u);
+    tc_mma(tm_im, a_rl, b_ih, 1u);
+    tc_mma(tm_im, a_ih, b_rh, 1u);   // Im A Re B
+    tc_mma(tm_im, a_ih, b_rl, 1u);
+    tc_mma(tm_im, a_il, b_rh, 1u);
+  }
+}
+
+// Kept out of line so that its registers do not weigh on the callers'.
+template <int TA, int TB>
+static __device__ __noinline__ void cgemm_tc(int M, int N, int K, cplx<float> alpha, const cplx<float> *A, int lda,
+                                             const cplx<float> *B, int ldb, cplx<float> beta, cplx<float> *C,
+                                             int ldc) {
   float *st = g_tc.stage;
-  float *arh = st, *arl = st + kTcM * kTcK, *aih = st + 2 * kTcM * kTcK, *ail = st + 3 * kTcM * kTcK;
-  float *nih = st + 4 * kTcM * kTcK, *nil = st + 5 * kTcM * kTcK;
-  float *brh = st + 6 * kTcM * kTcK, *brl = brh + kTcN * kTcK, *bih = brl + kTcN * kTcK, *bil = bih + kTcN * kTcK;
   const uint32_t tm_re = g_tc.tmem, tm_im = g_tc.tmem + kTcN;
-  const uint32_t bar = smem_u32(&g_tc.bar);
+  const uint32_t bar0 = smem_u32(&g_tc.bar[0]), bar1 = smem_u32(&g_tc.bar[1]);
   uint32_t phase = g_tc.phase;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool beta0 = beta.re == 0.f && beta.im == 0.f;
+  const int nk = (K + kTcK - 1) / kTcK;
   bool ok = true;
+  uint32_t pending = 0;  // bit b: buffer b holds committed MMAs not yet waited on
   for (int i0 = 0; i0 < M && ok; i0 += kTcM) {
     for (int j0 = 0; j0 < N && ok; j0 += kTcN) {
-      for (int k0 = 0; k0 < K; k0 += kTcK) {
-        for (int e = threadIdx.x; e < kTcM * kTcK; e += kThreads) {
-          int i, k;
-          if (TA == 0) { k = e % kTcK; i = e / kTcK; } else { i = e % kTcM; k = e / kTcM; }
-          const int gi = i0 + i, gk = k0 + k;
-          cplx<float> v = cmake<float>(0.f, 0.f);
-          if (gi < M && gk < K)
-            v = TA == 0 ? A[static_cast<int64_t>(gi) * lda + gk] : cconj(A[static_cast<int64_t>(gk) * lda + gi]);
-          const int o = tc_index(i, k);
-          const float rh = tf32_round(v.re), ih = tf32_round(v.im);
-          const float rl = tf32_round(v.re - rh), il = tf32_round(v.im - ih);
-          arh[o] = rh; arl[o] = rl; aih[o] = ih; ail[o] = il; nih[o] = -ih; nil[o] = -il;
+      for (int kc = 0; kc < nk; ++kc) {
+        const int b = kc & 1;
+        bool waited = true;
+        if (pending & (1u << b)) {  // the MMAs of chunk kc - 2 still read this buffer
+          waited = tc_wait(b ? bar1 : bar0, (phase >> b) & 1u);
+          phase ^= 1u << b;
+          pending &= ~(1u << b);
         }
-        for (int e = threadIdx.x; e < kTcN * kTcK; e += kThreads) {
-          int j, k;
-          if (TB == 0) { j = e % kTcN; k = e / kTcN; } else { k = e % kTcK; j = e / kTcK; }
-          const int gj = j0 + j, gk = k0 + k;
-          cplx<float> v = cmake<float>(0.f, 0.f);
-          if (gj < N && gk < K)
-            v = TB == 0 ? B[static_cast<int64_t>(gk) * ldb + gj] : cconj(B[static_cast<int64_t>(gj) * ldb + gk]);
-          const int o = tc_index(j, k);
-          const float rh = tf32_round(v.re), ih = tf32_round(v.im);
-          brh[o] = rh; brl[o] = tf32_round(v.re - rh); bih[o] = ih; bil[o] = tf32_round(v.im - ih);
-        }
+        float *buf = st + b * kTcBufFloats;
+        if (waited) tc_stage<TA, TB>(buf, M, N, K, A, lda, B, ldb, i0, j0, kc * kTcK);
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n");
-        __syncthreads();
+        const int failed = __syncthreads_or(waited ? 0 : 1);
         asm volatile("tcgen05.fence::after_thread_sync;\n");
-        if (threadIdx.x == 0) {
-#pragma unroll
-          for (int q = 0; q < kTcK / 8; ++q) {
-            const uint32_t acc = (k0 > 0 || q > 0) ? 1u : 0u;
-            const uint64_t a_rh = tc_desc(arh, q), a_rl = tc_desc(arl, q), a_ih = tc_desc(aih, q),
-                           a_il = tc_desc(ail, q), a_nh = tc_desc(nih, q), a_nl = tc_desc(nil, q);
-            const uint64_t b_rh = tc_desc(brh, q), b_rl = tc_desc(brl, q), b_ih = tc_desc(bih, q),
-                           b_il = tc_desc(bil, q);
-            tc_mma(tm_re, a_rh, b_rh, acc);  // Re A Re B
-            tc_mma(tm_re, a_rh, b_rl, 1u);
-            tc_mma(tm_re, a_rl, b_rh, 1u);
-            tc_mma(tm_re, a_nh, b_ih, 1u);   // - Im A Im B
-            tc_mma(tm_re, a_nh, b_il, 1u);
-            tc_mma(tm_re, a_nl, b_ih, 1u);
-            tc_mma(tm_im, a_rh, b_ih, acc);  // Re A Im B
-            tc_mma(tm_im, a_rh, b_il, 1u);
-            tc_mma(tm_im, a_rl, b_ih, 1u);
-            tc_mma(tm_im, a_ih, b_rh, 1u);   // Im A Re B
-            tc_mma(tm_im, a_ih, b_rl, 1u);
-            tc_mma(tm_im, a_il, b_rh, 1u);
-          }
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
-                       : "memory");
-        }
-        if (!tc_wait(bar, phase) && lane == 0) atomicExch(&g_tc.failed, 1);
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;\n");
-        __syncthreads();
-        if (g_tc.failed) {
+        if (failed) {
           ok = false;
           break;
         }
+        if (threadIdx.x == 0) {
+          tc_issue_chunk(buf, tm_re, tm_im, kc == 0);
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                           b ? bar1 : bar0)
+                       : "memory");
+        }
+        pending |= 1u << b;
       }
       if (!ok) break;
+      // the tile's last MMAs (and the older chunk in the other buffer)
+      bool waited = true;
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+        if (pending & (1u << b)) {
+          waited = tc_wait(b ? bar1 : bar0, (phase >> b) & 1u) && waited;
+          phase ^= 1u << b;
+        }
+      pending = 0;
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+      if (__syncthreads_or(waited ? 0 : 1)) {
+        ok = false;
+        break;
+      }
       // epilogue: warp w reads lanes 32 (w % 4) .. + 31, columns 16 (w / 4) .. + 15,
       // eight at a time
       const int quarter = warp & 3;
@@ -389,6 +459,15 @@ static __device__ void cgemm_tc(int M, int N, int K, cplx<float> alpha, const cp
       asm volatile("tcgen05.fence::after_thread_sync;\n");
     }
   }
+  if (!ok) {  // give the MMAs in flight a last bounded chance to land, then report
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+      if (pending & (1u << b)) {
+        tc_wait(b ? bar1 : bar0, (phase >> b) & 1u);
+        phase ^= 1u << b;
+      }
+    if (threadIdx.x == 0) g_tc.failed = 1;
+  }
   if (threadIdx.x == 0) g_tc.phase = phase;
   __syncthreads();
 }
@@ -402,7 +481,7 @@ static __device__ void cgemm(int M, int N, int K, cplx<T> alpha, const cplx<T> *
                       const cplx<T> *B, int ldb, cplx<T> beta, cplx<T> *C, int ldc,
                       cplx<T> *tile) {
   if constexpr (sizeof(T) == 4) {
-    if (g_tc.enabled && M >= 64 && N >= 32 && K >= 32) {
+    if (g_tc.enabled && M >= 64 && N >= 32 && K >= kTcK) {
       cgemm_tc<TA, TB>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
       return;
     }
@@ -629,63 +708,88 @@ static __device__ void qr_r_inplace(int m, int n, cplx<T> *B, int ld, cplx<T> *p
       continue;
     }
     wy_t_factor<T>(mr, jb, nb, ldv, Vp, Tm, G);
-    // trailing columns: b <- b - V (T^dag (V^dag b)); rows go four at a
-    // time so that four loads per thread are in flight
-    for (int c = j0 + jb + tid(); c < n; c += kThreads) {
-      cplx<T> w[kQrPanel];
+    // trailing columns: b <- b - V (T^dag (V^dag b)).  The nt trailing
+    // columns go to the warps in groups of cpw = 32 / ns consecutive columns
+    // (coalesced row reads), and the ns lanes that share a column split its
+    // rows (rows s, s + ns, s + 2 ns, ... for slice s); their partials of
+    // w = V^dag b are summed by shuffles, so that a trailing matrix of a few
+    // hundred columns still occupies the whole CTA.  Rows go four at a time
+    // so that four loads per thread are in flight.
+    {
+      const int nt = n - j0 - jb;
+      int ns = 1;
+      while (ns < 8 && nt * 2 * ns <= kThreads) ns *= 2;
+      const int cpw = 32 / ns, s = lane_id() / cpw;
+      for (int cb = j0 + jb + warp_id() * cpw; cb < n; cb += kWarps * cpw) {  // warp-uniform trip count
+        const int c = cb + lane_id() % cpw;
+        const bool valid = c < n;
+        cplx<T> w[kQrPanel];
 #pragma unroll
-      for (int k = 0; k < kQrPanel; ++k) w[k] = cmake<T>(0, 0);
-      int i = 0;
-      for (; i + 4 <= mr; i += 4) {
-        cplx<T> b[4];
+        for (int k = 0; k < kQrPanel; ++k) w[k] = cmake<T>(0, 0);
+        if (valid) {
+          int i = s;
+          for (; i + 3 * ns < mr; i += 4 * ns) {
+            cplx<T> b[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) b[u] = B[static_cast<int64_t>(j0 + i + u) * ld + c];
+            for (int u = 0; u < 4; ++u) b[u] = B[static_cast<int64_t>(j0 + i + u * ns) * ld + c];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int k = 0; k < kQrPanel; ++k)
-            if (k < jb) cfma(w[k], cconj(Vp[(i + u) * ldv + k]), b[u]);
-      }
-      for (; i < mr; ++i) {
-        const cplx<T> b = B[static_cast<int64_t>(j0 + i) * ld + c];
+              for (int k = 0; k < kQrPanel; ++k)
+                if (k < jb) cfma(w[k], cconj(Vp[(i + u * ns) * ldv + k]), b[u]);
+          }
+          for (; i < mr; i += ns) {
+            const cplx<T> b = B[static_cast<int64_t>(j0 + i) * ld + c];
 #pragma unroll
-        for (int k = 0; k < kQrPanel; ++k)
-          if (k < jb) cfma(w[k], cconj(Vp[i * ldv + k]), b);
-      }
-      // w <- T^dag w in place, highest index first: w'[a] = sum_{b<=a} conj(T[b][a]) w[b]
-#pragma unroll
-      for (int a = kQrPanel - 1; a >= 0; --a) {
-        if (a >= jb) continue;
-        cplx<T> acc = cmake<T>(0, 0);
-#pragma unroll
-        for (int b = 0; b <= a; ++b) cfma(acc, cconj(Tm[b * nb + a]), w[b]);
-        w[a] = acc;
-      }
-      for (i = 0; i + 4 <= mr; i += 4) {
-        cplx<T> b[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) b[u] = B[static_cast<int64_t>(j0 + i + u) * ld + c];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
+            for (int k = 0; k < kQrPanel; ++k)
+              if (k < jb) cfma(w[k], cconj(Vp[i * ldv + k]), b);
+          }
+        }
+        for (int off = cpw; off < 32; off *= 2)
 #pragma unroll
           for (int k = 0; k < kQrPanel; ++k)
             if (k < jb) {
-              const cplx<T> t = cmul(Vp[(i + u) * ldv + k], w[k]);
-              b[u] = cmake<T>(b[u].re - t.re, b[u].im - t.im);
+              w[k].re += __shfl_xor_sync(0xffffffffu, w[k].re, off);
+              w[k].im += __shfl_xor_sync(0xffffffffu, w[k].im, off);
             }
-          B[static_cast<int64_t>(j0 + i + u) * ld + c] = b[u];
-        }
-      }
-      for (; i < mr; ++i) {
-        cplx<T> &bref = B[static_cast<int64_t>(j0 + i) * ld + c];
-        cplx<T> acc = bref;
+        // w <- T^dag w in place, highest index first: w'[a] = sum_{b<=a} conj(T[b][a]) w[b]
 #pragma unroll
-        for (int k = 0; k < kQrPanel; ++k)
-          if (k < jb) {
-            const cplx<T> t = cmul(Vp[i * ldv + k], w[k]);
-            acc = cmake<T>(acc.re - t.re, acc.im - t.im);
+        for (int a = kQrPanel - 1; a >= 0; --a) {
+          if (a >= jb) continue;
+          cplx<T> acc = cmake<T>(0, 0);
+#pragma unroll
+          for (int b = 0; b <= a; ++b) cfma(acc, cconj(Tm[b * nb + a]), w[b]);
+          w[a] = acc;
+        }
+        if (valid) {
+          int i = s;
+          for (; i + 3 * ns < mr; i += 4 * ns) {
+            cplx<T> b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) b[u] = B[static_cast<int64_t>(j0 + i + u * ns) * ld + c];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+#pragma unroll
+              for (int k = 0; k < kQrPanel; ++k)
+                if (k < jb) {
+                  const cplx<T> t = cmul(Vp[(i + u * ns) * ldv + k], w[k]);
+                  b[u] = cmake<T>(b[u].re - t.re, b[u].im - t.im);
+                }
+              B[static_cast<int64_t>(j0 + i + u * ns) * ld + c] = b[u];
+            }
           }
-        bref = acc;
+          for (; i < mr; i += ns) {
+            cplx<T> &bref = B[static_cast<int64_t>(j0 + i) * ld + c];
+            cplx<T> acc = bref;
+#pragma unroll
+            for (int k = 0; k < kQrPanel; ++k)
+              if (k < jb) {
+                const cplx<T> t = cmul(Vp[i * ldv + k], w[k]);
+                acc = cmake<T>(acc.re - t.re, acc.im - t.im);
+              }
+            bref = acc;
+          }
+        }
       }
     }
     __syncthreads();
@@ -2526,6 +2630,52 @@ cudaError_t launch_dense_check_t(int what, int m, int n, void *A, void *V, void 
   if (e != cudaSuccess) return e;
   dense_check_kernel<T><<<1, kThreads, smem, s>>>(what, m, n, static_cast<cplx<T> *>(A),
                                                   static_cast<cplx<T> *>(V), static_cast<T *>(sig2), use_smem);
+  return cudaGetLastError();
+}
+
+// The sweeps' complex contraction alone on one CTA: C = alpha op(A) op(B) +
+// beta C through cgemm, with the tensor cores set up as the round kernel
+// sets them up (complex64 and use_tc) or disabled.  *status becomes
+// STN_ETIMEOUT if a tensor-core wait ran out.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1) dense_gemm_kernel(int ta, int tb, int m, int n, int k, cplx<T> alpha,
+                                                                 const cplx<T> *A, int lda, const cplx<T> *B, int ldb,
+                                                                 cplx<T> beta, cplx<T> *C, int ldc, int use_tc,
+                                                                 int *status) {
+  extern __shared__ __align__(16) char smem_raw[];
+  cplx<T> *tile = reinterpret_cast<cplx<T> *>(smem_raw);
+  float *stage = reinterpret_cast<float *>(tile + kBK * (kBM + kPad + kBN + kPad));
+  bool tc = false;
+  if constexpr (sizeof(T) == 4) tc = use_tc != 0;
+  if (tc) tc_setup(stage);
+  else tc_disable();
+  if (ta == 0 && tb == 0) cgemm<T, 0, 0>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tile);
+  else if (ta == 0) cgemm<T, 0, 1>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tile);
+  else if (tb == 0) cgemm<T, 1, 0>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tile);
+  else cgemm<T, 1, 1>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tile);
+  if (tc) {
+    if (threadIdx.x == 0 && g_tc.failed) *status = STN_ETIMEOUT;
+    tc_teardown();
+  }
+}
+
+template <typename T>
+cudaError_t launch_dense_gemm_t(int ta, int tb, int m, int n, int k, const double *alpha, const void *A, int lda,
+                                const void *B, int ldb, const double *beta, void *C, int ldc, int use_tc, int *status,
+                                cudaStream_t s) {
+  size_t smem = sizeof(cplx<T>) * kBK * (kBM + kPad + kBN + kPad);
+  if (sizeof(T) == 4 && use_tc) smem += sizeof(float) * kTcStageFloats;
+  cudaError_t e = cudaFuncSetAttribute(dense_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  cplx<T> al, be;
+  al.re = static_cast<T>(alpha[0]);
+  al.im = static_cast<T>(alpha[1]);
+  be.re = static_cast<T>(beta[0]);
+  be.im = static_cast<T>(beta[1]);
+  dense_gemm_kernel<T><<<1, kThreads, smem, s>>>(ta, tb, m, n, k, al, static_cast<const cplx<T> *>(A), lda,
+                                                 static_cast<const cplx<T> *>(B), ldb, be, static_cast<cplx<T> *>(C),
+                                                 ldc, use_tc, status);
   return cudaGetLastError();
 }
 

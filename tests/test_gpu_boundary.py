@@ -125,3 +125,27 @@ def test_captured_batch_replays_equal_plain_batches():
         _, ref, _ = gpu_run(w, shots, offset, theta)
         assert np.array_equal(got["records"], ref["records"])
         assert np.array_equal(got["born"], ref["born"])
+
+
+def test_shot_queue_matches_small_batches():
+    """A batch of more shots than the grid has CTAs (one per SM; the round
+    kernel then takes the shots from a queue in the order CTAs finish) gives
+    the records and Born probabilities of the same global shots run in small
+    batches: each shot's randomness is keyed by its global index."""
+    w = D3_EXACT.with_(p=0.02, rounds=1)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 2 * sms + 17
+    sim = stn.Simulator(w, max_shots=n)
+    theta = theta_table(w, sim.n_pairs)
+    big = sim.sample_shots(n, 0, theta)
+    sim.close()
+    small = stn.Simulator(w, max_shots=64)
+    recs, born = [], []
+    for off in range(0, n, 64):
+        k = min(64, n - off)
+        out = small.sample_shots(k, off, theta)
+        recs.append(out["records"][:k])
+        born.append(out["born"][:k])
+    small.close()
+    assert np.array_equal(big["records"], np.concatenate(recs))
+    assert np.array_equal(big["born"], np.concatenate(born))

@@ -247,3 +247,32 @@ def test_complex64_with_fp64_svds_parity():
     for s in range(shots):
         ref = run_shot(w, s, theta, prog)
         compare_shot(sim, out, s, ref, 1e-5, check_tableau=False)
+
+
+def test_complex64_gemm_units_agree_at_large_bonds():
+    """The two contraction units of the complex64 kernel (tcgen05 tensor
+    cores with the TF32 3-term split, and the CUDA cores) on the benchmark
+    workload for two rounds at chi cap 64, where the sweeps' products reach
+    the tensor-core tile sizes (the d=3 cases stay at chi <= 16, below them):
+    records identical up to near-threshold draws, Born probabilities within
+    1e-5 relative.  The oracle comparison at these bonds is the whole-shot
+    d=5 golden test."""
+    w = D5_BENCH.with_(rounds=2, chi_cap=64)
+    shots = 4
+    outs = []
+    for units in (stn.GEMM_TENSOR, stn.GEMM_FMA):
+        sim = stn.Simulator(w, max_shots=shots, gemm_units=units)
+        theta = theta_table(w, sim.n_pairs)
+        outs.append(sim.sample_shots(shots, 0, theta))
+        sim.close()
+    tc, fma = outs
+    assert max(tc["max_chi"]) == 64 and max(fma["max_chi"]) == 64
+    for s in range(shots):
+        a, b = tc["bits"][s], fma["bits"][s]
+        diff = next((i for i in range(len(a)) if a[i] != b[i]), None)
+        upto = len(a) if diff is None else diff
+        if diff is not None:
+            assert tc["near_draws"][s] > 0 or fma["near_draws"][s] > 0, f"shot {s}: record {diff} differs"
+        rb = fma["born"][s][:upto]
+        err = np.abs(tc["born"][s][:upto] - rb) / np.maximum(rb, 1e-4)
+        assert np.all(err < 1e-5), f"shot {s}: max rel Born difference {err.max():.3e}"

@@ -178,3 +178,32 @@ def test_layout_entry_point(lib):
         lay = build_layout(d)
         assert [tuple(v) for v in xy] == lay.coords
         assert [k for k in kind] == ["D" if q in lay.data else lay.kind[q] for q in range(lay.n)]
+
+
+def test_gemm_units_validated(lib):
+    """stn_config.gemm_units accepts STN_GEMM_TENSOR and STN_GEMM_FMA only."""
+    import ctypes
+    counts = np.zeros(5, dtype=np.int32)
+    for units, ok in ((stn.GEMM_TENSOR, True), (stn.GEMM_FMA, True), (2, False), (-1, False)):
+        cfg = stn.config_from_workload(D3_EXACT)
+        cfg.gemm_units = units
+        st = lib.stn_compile_program(ctypes.byref(cfg), counts.ctypes.data_as(ctypes.c_void_p), None, None)
+        assert (st == stn.STN_OK) == ok, (units, st)
+
+
+def test_dense_cgemm_rejects_bad_arguments(lib):
+    """stn_dense_cgemm validates sizes, strides, ops and units before any
+    launch (no GPU needed)."""
+    import ctypes
+    one = (ctypes.c_double * 2)(1.0, 0.0)
+    p = ctypes.c_void_p(16)  # never dereferenced: every call below is rejected first
+    good = dict(precision=1, units=0, op_a=0, op_b=0, m=8, n=8, k=8, lda=8, ldb=8, ldc=8)
+    bad = [dict(precision=2), dict(units=3), dict(op_a=2), dict(m=0), dict(k=5000), dict(lda=7),
+           dict(op_a=1, m=9, lda=8), dict(ldb=4), dict(ldc=7)]
+    for b in bad:
+        a = {**good, **b}
+        st = lib.stn_dense_cgemm(a["precision"], a["units"], a["op_a"], a["op_b"], a["m"], a["n"], a["k"], one, p,
+                                 a["lda"], p, a["ldb"], one, p, a["ldc"], p, None)
+        assert st == stn.STN_EINVAL, b
+    st = lib.stn_dense_cgemm(1, 0, 0, 0, 8, 8, 8, one, None, 8, p, 8, one, p, 8, p, None)
+    assert st == stn.STN_EINVAL
