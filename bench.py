@@ -64,9 +64,9 @@ def parse(argv=None):
     ap.add_argument("--precision", default="c64", choices=["c64", "c128", "c64-svd64"],
                     help="c128: the plain per-shot complex128 GPU path on the same workload (comparator); "
                          "c64-svd64: complex64 contractions with every bond SVD in FP64")
-    ap.add_argument("--gemm", default="tensor", choices=["tensor", "fma"],
-                    help="complex64 contraction units: tcgen05 tensor cores (TF32 3-term split, FP32 "
-                         "accumulation) or the CUDA cores")
+    ap.add_argument("--gemm", default="fma", choices=["fma", "tensor"],
+                    help="complex64 contraction units: the CUDA cores (FP32 FMA, the default) or the tcgen05 "
+                         "tensor cores (TF32 3-term split, FP32 accumulation)")
     ap.add_argument("--dense-routines", action="store_true",
                     help="time the truncation sweep's dense routines alone on one CTA and exit")
     return ap.parse_args(argv)
@@ -440,7 +440,10 @@ def main():
                                 "svds_large_bond": dprof["svd_count_large"] / shot_segs,
                                 "gauge_sites": dprof["gauge_sites"] / shot_segs,
                                 "jacobi_sweeps_per_large_svd": dprof["jacobi_sweeps_large"]
-                                / max(1.0, dprof["svd_count_large"])},
+                                / max(1.0, dprof["svd_count_large"]),
+                                "jacobi_rows_mean": dprof["jacobi_rows_large"] / max(1.0, dprof["svd_count_large"]),
+                                "jacobi_cols_mean": dprof["jacobi_cols_large"] / max(1.0, dprof["svd_count_large"]),
+                                "jacobi_rows_le_256_cycle_share": round(dprof["jacobi_rows256_cycles"] / loop, 4)},
               "source": "stn_profile_counters: SM clock cycles of each CTA per phase over the timed steps"}
     if clk and clk.get("sm_mhz"):
         # cycles the CTAs spent in their op loops over the cycles the launches

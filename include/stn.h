@@ -61,7 +61,7 @@ enum { STN_PAIRS_ADJACENT_IDLE = 0, STN_PAIRS_ADJACENT_IDLE_DIAG_XX = 1 };
 enum { STN_PRECISION_C128 = 0, STN_PRECISION_C64 = 1, STN_PRECISION_C64_SVD64 = 2 };
 enum { STN_BASIS_Z = 0, STN_BASIS_X = 1 };
 enum { STN_LAYERS_IDLE = 0xFF }; /* pair_layer_mask entry: use the idle rule */
-enum { STN_GEMM_TENSOR = 0, STN_GEMM_FMA = 1 }; /* stn_config.gemm_units */
+enum { STN_GEMM_FMA = 0, STN_GEMM_TENSOR = 1 }; /* stn_config.gemm_units */
 
 /* Simulation parameters: the problem statement of Sec. II-III (code
  * distance, rounds, CNOT schedule, crosstalk pairs and angles, Pauli noise
@@ -111,12 +111,16 @@ typedef struct {
                             this many bytes, and a sweep that needs more stops
                             its shot with STN_EOVERFLOW (reported by the next
                             synchronising call) */
-  int32_t gemm_units;      /* STN_GEMM_TENSOR (0): complex64 contractions of at
-                            least 64 x 32 x 16 run on the tcgen05 tensor cores
-                            (TF32 operands split into head and tail, FP32
-                            accumulation: FP32-accurate products);
-                            STN_GEMM_FMA (1): every contraction on the CUDA
-                            cores.  Complex128 always uses the CUDA cores */
+  int32_t gemm_units;      /* STN_GEMM_FMA (0, the default): every contraction
+                            on the CUDA cores (FP32 FMA for complex64);
+                            STN_GEMM_TENSOR (1): complex64 contractions of at
+                            least 64 x 32 x 16 on the tcgen05 tensor cores
+                            (TF32 operands split into head and tail, about 22
+                            bits each, FP32 accumulation).  The split's
+                            products are a few times less accurate than FP32
+                            FMA ones, and the sweeps carry that into the Born
+                            probabilities.  Complex128 always uses the CUDA
+                            cores */
 } stn_config;
 
 /* Per-shot diagnostics of the last batch (Sec. IV B: truncation). */
@@ -250,7 +254,7 @@ stn_status stn_compile_detectors(const stn_config *cfg, int32_t *h_counts, int32
 stn_status stn_algorithmic_flops(stn_ctx *ctx, double *h_total);
 
 /* Phase counters of all round launches since creation, summed over shot
- * slots (synchronises).  h_out[12]: SM clock cycles spent by the CTAs in
+ * slots (synchronises).  h_out[15]: SM clock cycles spent by the CTAs in
  * [0] the left (R-factor) sweep, [1] the right sweep's SVDs, [2] the rest of
  * the right sweep (contractions, sorting, new sites), [3] expectation values,
  * [4] the whole op loop (so [4] - [0..3] - [7] is the tableau and
@@ -259,8 +263,10 @@ stn_status stn_algorithmic_flops(stn_ctx *ctx, double *h_total);
  * that move the orthogonality centre into an operator's support and [8] the
  * number of sites they crossed; [9] the cycles of the shared-memory SVDs
  * (a part of [1]); [10] the Jacobi sweeps of the large-bond SVDs and [11]
- * the cycles of their Householder R factors (a part of [1]).  Diagnostics
- * only: they explain
+ * the cycles of their Householder R factors (a part of [1]); [12] and [13]
+ * the summed rows and columns of the matrices those Jacobi runs rotate, and
+ * [14] the cycles of the runs on at most 256 rows (a part of [1]).
+ * Diagnostics only: they explain
  * where a round's time goes, they are not part of the path. */
 stn_status stn_profile_counters(stn_ctx *ctx, double *h_out);
 
@@ -414,9 +420,9 @@ stn_status stn_dense_gemm_tc(int32_t m, int32_t n, int32_t k, const float *d_a, 
  * k x n, lda / ldb / ldc the row strides of A, B, C as stored (lda >= k for
  * op_a = 0, >= m for op_a = 1; likewise ldb; ldc >= n); each of m, n, k in
  * 1..4096.  alpha and beta: host (re, im) pairs, rounded to the precision.
- * gemm_units as in stn_config: STN_GEMM_TENSOR runs complex64 products of at
- * least 64 x 32 x 16 on the tcgen05 tensor cores (TF32 3-term split, FP32
- * accumulation), STN_GEMM_FMA (and complex128) on the CUDA cores.
+ * gemm_units as in stn_config: STN_GEMM_FMA (and complex128) on the CUDA
+ * cores, STN_GEMM_TENSOR runs complex64 products of at least 64 x 32 x 16 on
+ * the tcgen05 tensor cores (TF32 3-term split, FP32 accumulation).
  * *d_status (device int, caller-zeroed) becomes STN_ETIMEOUT if a bounded
  * wait for the tensor cores ran out.  Asynchronous on cuda_stream.
  * Errors: STN_EINVAL on bad sizes, strides, ops or null pointers, STN_ECUDA

@@ -14,7 +14,7 @@ import numpy as np
 from ._native import Config, ShotStats, build, load
 
 STN_OK, STN_EINVAL, STN_ENOMEM, STN_ECUDA, STN_ETIMEOUT, STN_ENUMERIC, STN_ENOTIMPL, STN_EOVERFLOW = range(8)
-GEMM_TENSOR, GEMM_FMA = 0, 1  # stn_config.gemm_units
+GEMM_FMA, GEMM_TENSOR = 0, 1  # stn_config.gemm_units
 PAIR_RULES = {"adjacent_idle": 0, "adjacent_idle+diag_xx": 1}
 OP_KINDS = {1: "RN", 2: "H", 3: "D1", 4: "CX", 5: "D2", 6: "ROT", 7: "M"}
 
@@ -76,10 +76,10 @@ def layout(distance):
 class Simulator:
     """One stn_ctx: a compiled program plus device state for max_shots shots.
     arena_cap_bytes > 0 caps each resident shot's stack of span tensors;
-    gemm_units picks the complex64 contraction units (GEMM_TENSOR: tcgen05
-    tensor cores, GEMM_FMA: CUDA cores; see stn_config)."""
+    gemm_units picks the complex64 contraction units (GEMM_FMA, the default:
+    CUDA cores; GEMM_TENSOR: tcgen05 tensor cores; see stn_config)."""
 
-    def __init__(self, workload, max_shots, stream=0, arena_cap_bytes=0, gemm_units=GEMM_TENSOR):
+    def __init__(self, workload, max_shots, stream=0, arena_cap_bytes=0, gemm_units=GEMM_FMA):
         self.lib = load()
         self.cfg = config_from_workload(workload)
         self.cfg.arena_cap_bytes = int(arena_cap_bytes)
@@ -189,7 +189,8 @@ class Simulator:
 
     PROFILE_KEYS = ("left_sweep_cycles", "svd_cycles", "right_sweep_rest_cycles", "expectation_cycles",
                     "op_loop_cycles", "svd_count_shared", "svd_count_large", "gauge_cycles",
-                    "gauge_sites", "svd_small_cycles", "jacobi_sweeps_large", "svd_qr_cycles")
+                    "gauge_sites", "svd_small_cycles", "jacobi_sweeps_large", "svd_qr_cycles",
+                    "jacobi_rows_large", "jacobi_cols_large", "jacobi_rows256_cycles")
 
     def profile_counters(self):
         """Per-phase SM cycles and SVD counts summed over shot slots since
@@ -320,7 +321,7 @@ def dense_gemm_tc(m, n, k, d_a, d_b, d_c, d_status, stream=0):
 
 
 def dense_cgemm(precision, op_a, op_b, m, n, k, d_a, lda, d_b, ldb, d_c, ldc, d_status, alpha=1.0, beta=0.0,
-                gemm_units=GEMM_TENSOR, stream=0):
+                gemm_units=GEMM_FMA, stream=0):
     """stn_dense_cgemm: d_c = alpha op(A) op(B) + beta d_c (row-major complex
     device buffers, op 0 = identity, 1 = conjugate transpose) on one CTA
     through the sweeps' contraction routine."""

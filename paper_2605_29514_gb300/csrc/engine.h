@@ -16,9 +16,10 @@ constexpr double kNearThreshold = 1e-5;
 // cycles and the number of sites they crossed; the cycles of the small SVDs
 // (a part of the SVD cycles); the Jacobi sweeps of the large-bond SVDs and
 // the cycles of their Householder R factors (a part of the SVD cycles).
-constexpr int kProfSlots = 12;
+constexpr int kProfSlots = 15;
 enum ProfSlot { PROF_LEFT = 0, PROF_SVD, PROF_RIGHT, PROF_EXPECT, PROF_OPS, PROF_NSVD_SMALL,
-                PROF_NSVD_LARGE, PROF_GAUGE, PROF_NGAUGE, PROF_SVD_SMALL, PROF_JSWEEPS, PROF_SVD_QR };
+                PROF_NSVD_LARGE, PROF_GAUGE, PROF_NGAUGE, PROF_SVD_SMALL, PROF_JSWEEPS, PROF_SVD_QR,
+                PROF_JROWS, PROF_JCOLS, PROF_JAC_ROWS256 };
 
 // Everything one segment launch needs.  Per-shot arrays are indexed by the
 // shot's position in the batch; per-CTA scratch by blockIdx.x.
