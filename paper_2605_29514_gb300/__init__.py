@@ -195,7 +195,7 @@ class Simulator:
     def profile_counters(self):
         """Per-phase SM cycles and SVD counts summed over shot slots since
         creation (see stn_profile_counters)."""
-        buf = (ctypes.c_double * 12)()
+        buf = (ctypes.c_double * len(self.PROFILE_KEYS))()  # the library writes one value per key
         self._check(self.lib.stn_profile_counters(self.ctx, ctypes.cast(buf, ctypes.c_void_p)))
         return dict(zip(self.PROFILE_KEYS, list(buf)))
 

@@ -1152,85 +1152,65 @@ static __device__ bool cross_visit_regs(int m, cplx<float> *C, int c0, int wI, i
     if (t == 0) *rot = 0;
   }
   __syncthreads();
-  // The 16 steps go in groups of four: within a group J's register slots are
-  // addressed at a compile-time offset u (slot b + u pairs with I_b at step
-  // 4 g + u), and J shifts by four slots once per group.  The 16-bit mask
-  // of the step's non-trivial rotations is published next to their
-  // parameters, so that a skipped pair costs one bit test.
-  unsigned *rmask = reinterpret_cast<unsigned *>(rot + 1);
-  for (int g = 0; g < 4; ++g) {
+  for (int step = 0; step < 16; ++step) {
+    float v[32];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int step = 4 * g + u;
-      float v[32];
+    for (int b = 0; b < 16; ++b) {
+      float gr = 0.f, gi = 0.f;
 #pragma unroll
-      for (int b = 0; b < 16; ++b) {
-        float gr = 0.f, gi = 0.f;
+      for (int r = 0; r < R; ++r) {
+        const cplx<float> x = xi[r][b], y = xj[r][b];
+        gr += x.re * y.re + x.im * y.im;  // conj(x) y
+        gi += x.re * y.im - x.im * y.re;
+      }
+      v[2 * b] = gr;
+      v[2 * b + 1] = gi;
+    }
+    const float s = cta_reduce32(v, red);
+    if (t < 32) {
+      const float gi = __shfl_down_sync(0xffffffffu, s, 1);
+      if ((t & 1) == 0) {
+        const int b = t >> 1, jb = (b + step) & 15;
+        const float gr = s, al = nrm[b], be = nrm[16 + jb];
+        float4 p = make_float4(1.f, 0.f, 1.f, 0.f);  // identity: skipped
+        if (al > negligible && be > negligible) {
+          const float absg = sqrtf(gr * gr + gi * gi);
+          if (absg > tol * sqrtf(al) * sqrtf(be)) {
+            const float zeta = (be - al) / (2.f * absg);
+            const float az = fabsf(zeta);
+            float tt = az > 1e10f ? 0.5f / az : 1.f / (az + sqrtf(1.f + zeta * zeta));
+            if (zeta < 0.f) tt = -tt;
+            const float cs = 1.f / sqrtf(1.f + tt * tt), sn = tt * cs;
+            p = make_float4(cs, sn, gr / absg, -gi / absg);  // conj(g / |g|)
+            nrm[b] = fmaxf(al - tt * absg, 0.f);
+            nrm[16 + jb] = fmaxf(be + tt * absg, 0.f);
+            *rot = 1;
+          }
+        }
+        prm[b] = p;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      const float4 p = prm[b];
+      if (p.x != 1.f || p.y != 0.f || p.z != 1.f || p.w != 0.f) {  // uniform over the CTA
+        const cplx<float> uc = cmake<float>(p.z, p.w);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          const cplx<float> x = xi[r][b], y = xj[r][(b + u) & 15];
-          gr += x.re * y.re + x.im * y.im;  // conj(x) y
-          gi += x.re * y.im - x.im * y.re;
-        }
-        v[2 * b] = gr;
-        v[2 * b + 1] = gi;
-      }
-      const float s = cta_reduce32(v, red);
-      if (t < 32) {
-        const float gi = __shfl_down_sync(0xffffffffu, s, 1);
-        bool turn = false;
-        if ((t & 1) == 0) {
-          const int b = t >> 1, jb = (b + step) & 15;
-          const float gr = s, al = nrm[b], be = nrm[16 + jb];
-          float4 p = make_float4(1.f, 0.f, 1.f, 0.f);  // identity: skipped
-          if (al > negligible && be > negligible) {
-            const float absg = sqrtf(gr * gr + gi * gi);
-            if (absg > tol * sqrtf(al) * sqrtf(be)) {
-              const float zeta = (be - al) / (2.f * absg);
-              const float az = fabsf(zeta);
-              float tt = az > 1e10f ? 0.5f / az : 1.f / (az + sqrtf(1.f + zeta * zeta));
-              if (zeta < 0.f) tt = -tt;
-              const float cs = 1.f / sqrtf(1.f + tt * tt), sn = tt * cs;
-              p = make_float4(cs, sn, gr / absg, -gi / absg);  // conj(g / |g|)
-              nrm[b] = fmaxf(al - tt * absg, 0.f);
-              nrm[16 + jb] = fmaxf(be + tt * absg, 0.f);
-              turn = true;
-            }
-          }
-          prm[b] = p;
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, turn);  // bit 2b: pair b rotates
-        if (t == 0) {
-          *rmask = bal;
-          if (bal) *rot = 1;
-        }
-      }
-      __syncthreads();
-      const unsigned msk = *rmask;
-#pragma unroll
-      for (int b = 0; b < 16; ++b) {
-        if (msk & (1u << (2 * b))) {  // uniform over the CTA
-          const float4 p = prm[b];
-          const cplx<float> uc = cmake<float>(p.z, p.w);
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const cplx<float> x = xi[r][b], y = cmul(uc, xj[r][(b + u) & 15]);
-            xi[r][b] = cmake<float>(p.x * x.re - p.y * y.re, p.x * x.im - p.y * y.im);
-            xj[r][(b + u) & 15] = cmake<float>(p.y * x.re + p.x * y.re, p.y * x.im + p.x * y.im);
-          }
+          const cplx<float> x = xi[r][b], y = cmul(uc, xj[r][b]);
+          xi[r][b] = cmake<float>(p.x * x.re - p.y * y.re, p.x * x.im - p.y * y.im);
+          xj[r][b] = cmake<float>(p.y * x.re + p.x * y.re, p.y * x.im + p.x * y.im);
         }
       }
     }
-    // slot b + 4 of J pairs with I_b at the next group: shift J by four slots
+    // slot b of J now pairs with I_b at the next step: shift J by one slot
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      cplx<float> head[4];
+      const cplx<float> first = xj[r][0];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) head[b] = xj[r][b];
-#pragma unroll
-      for (int b = 0; b < 12; ++b) xj[r][b] = xj[r][b + 4];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) xj[r][12 + b] = head[b];
+      for (int b = 0; b < 15; ++b) xj[r][b] = xj[r][b + 1];
+      xj[r][15] = first;
     }
   }
   __syncthreads();
