@@ -284,8 +284,13 @@ static __device__ void tc_teardown() {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(g_tc.tmem), "r"(kTcCols));
 }
 
+// Static shared memory starts with whatever the SM's previous kernel left
+// there, so a kernel without tensor memory clears both flags.
 static __device__ __forceinline__ void tc_disable() {
-  if (threadIdx.x == 0) g_tc.enabled = 0;
+  if (threadIdx.x == 0) {
+    g_tc.enabled = 0;
+    g_tc.failed = 0;
+  }
   __syncthreads();
 }
 
@@ -2294,6 +2299,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
   if constexpr (sizeof(T) == 4) tc_alloc = P.use_tc && static_cast<int64_t>(P.svd_elems) * 2 >= kTcStageFloats;
   if (tc_alloc) tc_setup(reinterpret_cast<float *>(S.jbuf));
   else tc_disable();
+  bool tc_live = tc_alloc;  // CTA-uniform
   // With a ticket counter the CTAs take the batch's shots in order as they
   // finish (a work queue that balances uneven shots when the batch holds
   // more shots than CTAs); without one, shots are grid-strided.
@@ -2326,13 +2332,20 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
     long long t_ops = clock64();
     const uint64_t gshot = (P.shot_offset_dev ? *P.shot_offset_dev : P.shot_offset) + static_cast<uint64_t>(shot);
     for (int oi = P.op_begin; oi < P.op_end; ++oi) {
-      if (g_tc.failed) {  // a tensor-core wait ran out: this shot stops, the rest use the CUDA cores
-        if (tid() == 0) {
-          S.misc[M_FAIL] = STN_ETIMEOUT;
-          g_tc.failed = 0;
-          g_tc.enabled = 0;
-        }
+      if (tc_live) {
+        // a tensor-core wait ran out: this shot stops, the rest use the CUDA
+        // cores.  Every thread reads the flag before thread 0 may clear it.
+        const int tc_failed = g_tc.failed;
         __syncthreads();
+        if (tc_failed) {
+          if (tid() == 0) {
+            S.misc[M_FAIL] = STN_ETIMEOUT;
+            g_tc.failed = 0;
+            g_tc.enabled = 0;
+          }
+          tc_live = false;
+          __syncthreads();
+        }
       }
       if (S.misc[M_FAIL]) break;
       const Op op = P.ops[oi];
