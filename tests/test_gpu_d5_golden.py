@@ -74,7 +74,8 @@ def test_whole_d5_shots_match_oracle(gpu_shots):
         assert np.all(err < 1e-4), f"shot {s}: max rel Born error {err.max():.3e} at record {int(err.argmax())}"
         if div is None:
             assert out["max_chi"][s] == meta[s]["max_chi"]
-            assert abs(out["logp"][s] - meta[s]["logp"]) < 1e-4 * max(1.0, abs(meta[s]["logp"]))
+            # each realised probability within 1e-4 relative moves log P by at most ~1e-4
+            assert abs(out["logp"][s] - meta[s]["logp"]) < 1e-4 * len(rec)
     print(f"max relative Born error over {len(rows)} whole shots: {worst:.3e}")
 
 
