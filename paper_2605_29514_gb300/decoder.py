@@ -179,6 +179,144 @@ class LookupDecoder:
         return out
 
 
+class MatchingDecoder:
+    """Minimum-weight perfect matching on the detector graph of a FaultModel
+    (the paper decodes with MWPM under the PTA error model, Sec. III C).
+
+    Graph: one node per detector plus a boundary node.  Each fault that flips
+    one detector (an edge to the boundary) or two (an edge between them) gives
+    an edge of weight log((1 - q) / q); parallel edges keep the likelier
+    fault.  Faults that flip more detectors (a Y, or a two-qubit Pauli that
+    acts on both check types) are products of such edges and add none.
+    uniform=True gives every edge weight 1, which makes the decoder a
+    nearest-explanation decoder: at distance d it corrects every set of
+    fewer than d / 2 faults, the property the CPU tests pin.
+
+    Decoding a syndrome: shortest paths between all nodes (Dijkstra) carry
+    their logical parity.  The fired detectors are matched in pairs or to
+    the boundary at least total path length: exactly by dynamic programming
+    over subsets for up to dp_limit defects, else by the blossom algorithm
+    (networkx.max_weight_matching, each defect with its own copy of the
+    boundary).  The predicted flip is the XOR of the matched paths'
+    parities.  Host-side and off the timed path."""
+
+    def __init__(self, model, uniform=False, dp_limit=12):
+        import scipy.sparse as sp
+        from scipy.sparse.csgraph import dijkstra
+        n = model.det.shape[1]
+        self.n_det, self.boundary = n, n
+        best = {}  # (a, b) -> (q, obs)
+        for f in range(len(model.prob)):
+            d = np.flatnonzero(model.det[f])
+            if len(d) == 0 or len(d) > 2:
+                continue
+            key = (int(d[0]), int(d[1])) if len(d) == 2 else (int(d[0]), n)
+            q = float(model.prob[f])
+            if q <= 0.0:
+                continue
+            if key not in best or q > best[key][0]:
+                best[key] = (q, bool(model.obs[f]))
+        rows, cols, wts = [], [], []
+        self._edge_obs = {}
+        for (a, b), (q, o) in best.items():
+            w = 1.0 if uniform else float(np.log((1.0 - q) / q)) if q < 0.5 else 1e-9
+            rows.append(a)
+            cols.append(b)
+            wts.append(max(w, 1e-9))
+            self._edge_obs[(a, b)] = self._edge_obs[(b, a)] = o
+        g = sp.coo_matrix((wts, (rows, cols)), shape=(n + 1, n + 1)).tocsr()
+        self.dist, pred = dijkstra(g, directed=False, return_predecessors=True)
+        # logical parity of each shortest path, walking the predecessor tree
+        par = np.zeros((n + 1, n + 1), dtype=bool)
+        for src in range(n + 1):
+            order = np.argsort(self.dist[src])
+            for v in order:
+                u = pred[src, v]
+                if u >= 0:
+                    par[src, v] = par[src, u] ^ self._edge_obs[(int(u), int(v))]
+        self.parity = par
+        self.dp_limit = int(dp_limit)
+        self.unmatched = 0
+
+    def _decode(self, defects):
+        k = len(defects)
+        if k == 0:
+            return 0
+        if k <= self.dp_limit:
+            return self._decode_dp(defects)
+        return self._decode_blossom(defects)
+
+    def _decode_dp(self, defects):
+        """Exact minimum-weight matching of a few defects by dynamic
+        programming over subsets: the lowest remaining defect either goes to
+        the boundary or pairs with one of the others."""
+        from functools import lru_cache
+        bd = [self.dist[a, self.boundary] for a in defects]
+        bp = [int(self.parity[a, self.boundary]) for a in defects]
+
+        @lru_cache(maxsize=None)
+        def best(mask):
+            if mask == 0:
+                return 0.0, 0
+            i = (mask & -mask).bit_length() - 1
+            rest = mask & ~(1 << i)
+            c, f = best(rest)
+            cand = (bd[i] + c, f ^ bp[i])
+            m2 = rest
+            while m2:
+                j = (m2 & -m2).bit_length() - 1
+                m2 &= m2 - 1
+                c2, f2 = best(rest & ~(1 << j))
+                v = self.dist[defects[i], defects[j]] + c2
+                if v < cand[0]:
+                    cand = (v, f2 ^ int(self.parity[defects[i], defects[j]]))
+            return cand
+
+        cost, flip = best((1 << len(defects)) - 1)
+        if not np.isfinite(cost):
+            self.unmatched += 1
+        return flip
+
+    def _decode_blossom(self, defects):
+        """The same matching for many defects: each defect with its own copy
+        of the boundary, perfect matching of least total path length by the
+        blossom algorithm (networkx)."""
+        import networkx as nx
+        k = len(defects)
+        big = 1.0 + 2.0 * np.nanmax(np.where(np.isfinite(self.dist), self.dist, 0.0)) * max(k, 1)
+        g = nx.Graph()
+        for i in range(k):
+            a = defects[i]
+            db = self.dist[a, self.boundary]
+            if np.isfinite(db):
+                g.add_edge(("d", i), ("b", i), weight=big - db)
+            for j in range(i + 1, k):
+                dab = self.dist[a, defects[j]]
+                if np.isfinite(dab):
+                    g.add_edge(("d", i), ("d", j), weight=big - dab)
+                g.add_edge(("b", i), ("b", j), weight=big)
+        match = nx.max_weight_matching(g, maxcardinality=True)
+        flip = 0
+        covered = 0
+        for u, v in match:
+            if u[0] == "b" and v[0] == "b":
+                continue
+            if u[0] == "b":
+                u, v = v, u
+            a = defects[u[1]]
+            b = self.boundary if v[0] == "b" else defects[v[1]]
+            flip ^= int(self.parity[a, b])
+            covered += 1 + (v[0] == "d")
+        if covered < k:
+            self.unmatched += 1
+        return flip
+
+    def predict(self, det_bits):
+        """Predicted logical flips of detector rows [shots, n_det] (0/1)."""
+        det_bits = np.asarray(det_bits, dtype=bool)
+        return np.array([self._decode(np.flatnonzero(row)) for row in det_bits], dtype=np.uint8)
+
+
 def logical_error_rate(decoder, det_bits, observed):
     """Fraction of shots whose predicted flip differs from the observed
     logical parity, and that count."""

@@ -15,7 +15,7 @@ import paper_2605_29514_gb300 as stn
 from paper_2605_29514_gb300.decoder import LookupDecoder, build_fault_model, wilson_interval
 from oracle.circuit import detectors, logical_z
 from oracle.shot import make_program, run_shot
-from workloads import D3_EXACT, theta_table
+from workloads import D3_EXACT, D5_BENCH, theta_table
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -88,3 +88,68 @@ def test_eq1_estimate_reduces_to_failure_rate_for_pauli_errors():
     c = np.array([0, 1, 1, 0])
     assert eq1_estimate(e, c) == 0.5  # shots 2 and 3 fail
     assert abs(eq1_estimate([np.cos(0.4)], [0]) - np.sin(0.2)) < 1e-15
+
+
+def _graphlike(model):
+    return [f for f in range(len(model.prob)) if 1 <= int(model.det[f].sum()) <= 2]
+
+
+@pytest.mark.parametrize("uniform", [True, False])
+@pytest.mark.parametrize("w", [D3_EXACT.with_(p=1e-3), D5_BENCH], ids=["d3", "d5"])
+def test_matching_corrects_every_single_fault(w, uniform):
+    """Minimum-weight matching on the PTA-plus-Pauli detector graph decodes
+    every single fault that flips one or two detectors to its own logical
+    effect: at distance d >= 3 any other explanation with a different
+    logical effect needs at least d - 1 >= 2 edges.  Also the empty syndrome
+    decodes to no flip."""
+    from paper_2605_29514_gb300.decoder import MatchingDecoder
+    theta = theta_table(w, stn.compile_program(w)[2].shape[0])
+    model = build_fault_model(w, theta)
+    dec = MatchingDecoder(model, uniform=uniform)
+    g = _graphlike(model)
+    assert len(g) > 0.5 * len(model.prob)
+    assert np.array_equal(dec.predict(model.det[g]), model.obs[g].astype(np.uint8))
+    assert dec.predict(np.zeros((1, model.det.shape[1]), dtype=bool))[0] == 0
+    assert dec.unmatched == 0
+
+
+@pytest.mark.parametrize("dp_limit", [12, 0])
+def test_matching_corrects_fault_pairs_at_distance_5(dp_limit):
+    """At d = 5 every pair of graph-like faults is corrected with unit
+    weights (another explanation with a different logical effect needs at
+    least 5 - 2 = 3 edges), through the subset dynamic program and, with
+    dp_limit = 0, through the blossom matching; 2,000 seeded pairs."""
+    from paper_2605_29514_gb300.decoder import MatchingDecoder
+    if dp_limit == 0:
+        pytest.importorskip("networkx")
+    w = D5_BENCH
+    theta = theta_table(w, stn.compile_program(w)[2].shape[0])
+    model = build_fault_model(w, theta)
+    dec = MatchingDecoder(model, uniform=True, dp_limit=dp_limit)
+    g = np.array(_graphlike(model))
+    rng = np.random.default_rng(5)
+    pairs = rng.choice(g, size=(2000, 2))
+    det = model.det[pairs[:, 0]] ^ model.det[pairs[:, 1]]
+    obs = model.obs[pairs[:, 0]] ^ model.obs[pairs[:, 1]]
+    assert np.array_equal(dec.predict(det), obs.astype(np.uint8))
+
+
+def test_matching_and_lookup_rates_agree_on_sampled_faults():
+    """On 3,000 syndromes sampled from the d = 3 fault model itself (each
+    fault fires independently with its probability), the matching decoder's
+    failure rate and the lookup table's lie in each other's 95% Wilson
+    intervals."""
+    from paper_2605_29514_gb300.decoder import MatchingDecoder
+    w = D3_EXACT.with_(p=1e-3)
+    theta = theta_table(w, stn.compile_program(w)[2].shape[0])
+    model = build_fault_model(w, theta)
+    rng = np.random.default_rng(1)
+    fire = (rng.random((3000, len(model.prob))) < model.prob).astype(np.uint8)
+    det = (fire @ model.det.astype(np.uint8)) % 2
+    obs = (fire @ model.obs.astype(np.uint8)) % 2
+    n = len(obs)
+    k_m = int(np.sum(MatchingDecoder(model).predict(det) != obs))
+    k_l = int(np.sum(LookupDecoder(model).predict(det) != obs))
+    lo_m, hi_m = wilson_interval(k_m, n)
+    lo_l, hi_l = wilson_interval(k_l, n)
+    assert lo_m <= k_l / n <= hi_m and lo_l <= k_m / n <= hi_l, (k_m, k_l)
