@@ -72,6 +72,14 @@ def parse(argv=None):
                          "the complex128 path on --shots shots (default 8) of the workload cut to --rounds rounds "
                          "at --chi-cap, print one JSON line per path and exit")
     ap.add_argument("--rounds", type=int, default=2, help="rounds of the --accuracy comparison")
+    ap.add_argument("--sweep", default=None, choices=["pauli", "pta", "coherent"],
+                    help="logical-error-rate sweep over --distances x --ps (rounds = distance), decoded by "
+                         "matching: Table I Pauli noise alone, plus the Pauli-twirled crosstalk (both sampled "
+                         "on the host from the fault model), or the coherent simulation on the GPU; one JSON "
+                         "line per point and the d-crossing, then exit")
+    ap.add_argument("--distances", default="3,5")
+    ap.add_argument("--ps", default="2e-3,5e-3,1e-2,2e-2")
+    ap.add_argument("--theta", type=float, default=None, help="crosstalk angle of the sweep (default the workload's)")
     ap.add_argument("--dense-routines", action="store_true",
                     help="time the truncation sweep's dense routines alone on one CTA and exit")
     return ap.parse_args(argv)
@@ -329,6 +337,25 @@ def accuracy(w, shots, rounds):
                           "max_chi": int(max(o["max_chi"]))}), flush=True)
 
 
+def threshold_sweep(w, args):
+    """The LER sweep of Sec. V (Fig. 4) through paper_2605_29514_gb300.sweep."""
+    import paper_2605_29514_gb300 as stn
+    from paper_2605_29514_gb300.sweep import coherent_sampler, crossing, sweep
+    stn.build()
+    ds = [int(x) for x in args.distances.split(",")]
+    ps = [float(x) for x in args.ps.split(",")]
+    shots = args.shots if args.shots > 0 else 4000
+    sim = coherent_sampler(max_shots=1024) if args.sweep == "coherent" else None
+    t0 = time.perf_counter()
+    pts = sweep(w, ds, ps, shots, noise=args.sweep, theta=args.theta, seed=1, simulate=sim,
+                angles=lambda ww, k: theta_table(ww, k))
+    for pt in pts:
+        print(json.dumps({"what": "ler_point", **pt.__dict__}), flush=True)
+    for a, b in zip(ds, ds[1:]):
+        print(json.dumps({"what": "crossing", "noise": args.sweep, "d_small": a, "d_large": b,
+                          "p": crossing(pts, a, b), "seconds": round(time.perf_counter() - t0, 1)}), flush=True)
+
+
 def dense_routines():
     """The Householder R factor and the one-sided Jacobi SVD variants of the
     truncation sweep (Sec. IV B) alone on one CTA, at sizes the sweep meets,
@@ -402,6 +429,9 @@ def main():
         return
     if args.accuracy:
         accuracy(w, args.shots if args.shots > 0 else 8, args.rounds)
+        return
+    if args.sweep:
+        threshold_sweep(w, args)
         return
     import torch
     import paper_2605_29514_gb300 as stn
