@@ -95,3 +95,40 @@ def test_d5_shot_against_tight_cutoff_oracle(gpu_shots):
         if div is not None:
             assert out["near_draws"][s] > 0 or meta[s]["near_draws"] > 0
         assert np.all(err < 1e-3)
+
+
+def _cap64_workload():
+    return D5_BENCH.with_(rounds=2, chi_cap=64, name="d5_r2_theta0.10_p1e-3_chi64_c64")
+
+
+@pytest.mark.parametrize("precision,bar", [(None, 5e-5), ("c128", 1e-7)])
+def test_d5_two_rounds_cap64_against_oracle(precision, bar):
+    """Whole shots of the benchmark workload cut to two rounds at chi cap 64
+    (tests/golden/oracle_d5_r2_cap64_records.txt, written from oracle/
+    alone): the bonds reach the cap in round 1, so the large-bond SVDs and
+    the large contractions run end to end.  Records identical except after a
+    near-threshold draw; Born probabilities within 5e-5 relative for the
+    complex64 path (its FP32 floor: 1.7e-5 against the complex128 path on
+    these shots) and 1e-7 for the complex128 path; the same largest bond."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from workloads import PRECISION_C128
+    rows, meta = load_golden("oracle_d5_r2_cap64_records.txt")
+    stn.build()
+    w = _cap64_workload()
+    if precision == "c128":
+        w = w.with_(precision=PRECISION_C128)
+    shots = max(rows) + 1
+    sim = stn.Simulator(w, max_shots=shots)
+    out = sim.sample_shots(shots, 0, theta_table(w, sim.n_pairs))
+    sim.close()
+    for s, (rec, born) in rows.items():
+        bits = list(out["bits"][s])
+        div = first_divergence(bits, rec)
+        upto = len(rec) if div is None else div
+        if div is not None:
+            assert out["near_draws"][s] > 0 or meta[s]["near_draws"] > 0, f"shot {s}: record {div} differs"
+        err = np.abs(out["born"][s][:upto] - born[:upto]) / np.maximum(born[:upto], 1e-4)
+        assert np.all(err < bar), f"shot {s}: max rel Born error {err.max():.3e} at record {int(err.argmax())}"
+        if div is None:
+            assert out["max_chi"][s] == meta[s]["max_chi"]
