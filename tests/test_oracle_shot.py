@@ -416,3 +416,24 @@ def test_adjoint_matches_central_differences(basis):
         tm[k] -= h
         fd = (forced_logprob(w, 3, tp, rec, prog) - forced_logprob(w, 3, tm, rec, prog)) / (2 * h)
         assert abs(g[k] - fd) < 1e-6 * max(1.0, abs(fd)), (k, g[k], fd)
+
+
+def test_random_pair_signs_are_sign_sensitive_but_twirl_alike():
+    """Eq. 9's random-sign crosstalk, read as one quenched sign per pair: the
+    table holds +-theta with both signs present; mixed signs change Born
+    probabilities (the global-sign invariance needs every sign flipped at
+    once), while the Pauli-twirled fault probabilities sin^2 theta are the
+    same as for the uniform table."""
+    from paper_2605_29514_gb300.decoder import build_fault_model
+    import paper_2605_29514_gb300 as stn
+    stn.build()
+    w = D3_EXACT.with_(rounds=2)
+    prog = make_program(w)
+    uni = theta_table(w, len(prog.pairs))
+    mixed = theta_table(w.with_(theta_sign="random_pair"), len(prog.pairs))
+    assert np.array_equal(np.abs(mixed), uni) and (mixed > 0).any() and (mixed < 0).any()
+    a = run_shot(w, 0, uni, prog)
+    b = run_shot(w, 0, mixed, prog)
+    n = min(i for i in range(len(a.record) + 1) if i == len(a.record) or a.record[i] != b.record[i])
+    assert np.max(np.abs(np.array(a.born[:n]) - np.array(b.born[:n]))) > 1e-6
+    assert np.allclose(build_fault_model(w, uni).prob, build_fault_model(w, mixed).prob, rtol=0, atol=0)

@@ -43,6 +43,9 @@ class Workload:
     pair_rule: str = "adjacent_idle"
     theta_sigma: float = 0.0
     theta_seed: int = 7
+    # Eq. 9's random-sign crosstalk: "fixed" keeps every angle's sign;
+    # "random_pair" draws one sign per pair from theta_seed (quenched).
+    theta_sign: str = "fixed"
     # Z or X memory; optional caller CNOT schedule (one 4-tuple of data
     # qubits or -1 per ancilla, ancillas in ascending qubit order) and
     # explicit crosstalk pairs ((a, b, 'ZZ' | 'XX', layer mask or None), in
@@ -66,11 +69,20 @@ class Workload:
 
 def theta_table(w, n_pairs):
     """Per-pair angles: uniform, or quenched N(theta, theta_sigma^2) from
-    theta_seed (independent of the shot seed)."""
+    theta_seed (independent of the shot seed); with theta_sign =
+    "random_pair", each pair's angle then takes a sign drawn from
+    theta_seed + 1."""
     if w.theta_sigma == 0.0:
-        return np.full(n_pairs, w.theta, dtype=np.float64)
-    rng = np.random.default_rng(w.theta_seed)
-    return rng.normal(w.theta, w.theta_sigma, size=n_pairs).astype(np.float64)
+        table = np.full(n_pairs, w.theta, dtype=np.float64)
+    else:
+        rng = np.random.default_rng(w.theta_seed)
+        table = rng.normal(w.theta, w.theta_sigma, size=n_pairs).astype(np.float64)
+    if w.theta_sign == "random_pair":
+        signs = np.random.default_rng(w.theta_seed + 1).integers(0, 2, size=n_pairs) * 2 - 1
+        table = table * signs
+    elif w.theta_sign != "fixed":
+        raise ValueError(f"unknown theta_sign {w.theta_sign!r}")
+    return table
 
 
 # d=3, 3 rounds, theta = 0.05 ZZ on idle adjacent pairs, no Pauli noise,
