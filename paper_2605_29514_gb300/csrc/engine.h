@@ -56,7 +56,7 @@ struct EngineParams {
   int work_c;               // largest bond of the plan (sizes the work area)
   int svd_elems;            // complex elements of the shared-memory SVD buffer
   int svd64_all;            // complex64 path: every bond SVD in double precision
-  int use_tc;               // complex64 path: large contractions on the tcgen05 tensor cores
+  int use_tc;               // complex64 and gemm_units = STN_GEMM_TENSOR: large contractions on tcgen05
   int *err;                 // first error code seen on the device
   int *ticket;              // shot queue of a launch (zeroed before it), or null: grid-stride
   // Adjoint of log P(record) (all null in an ordinary run).  forced: records

@@ -2293,8 +2293,9 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(EngineParams P) {
   const int n = P.n, W = P.W;
   Smem<T> S = carve<T>(smem_raw, n, W, P.svd_elems);
   Scratch<T> X = scratch_for<T>(P, P.work_c);
-  // complex64: the large contractions run on the tensor cores, staged in the
-  // shared SVD buffer (free whenever a GEMM runs)
+  // complex64 with use_tc (gemm_units = STN_GEMM_TENSOR): the large
+  // contractions run on the tensor cores, staged in the shared SVD buffer
+  // (free whenever a GEMM runs)
   bool tc_alloc = false;
   if constexpr (sizeof(T) == 4) tc_alloc = P.use_tc && static_cast<int64_t>(P.svd_elems) * 2 >= kTcStageFloats;
   if (tc_alloc) tc_setup(reinterpret_cast<float *>(S.jbuf));
