@@ -79,3 +79,39 @@ def test_crossing_interpolates_log_linearly():
     # gaps -0.01 and +0.01: the zero is halfway in log p
     assert x == pytest.approx(np.sqrt(1e-3 * 1e-2), rel=1e-12)
     assert crossing(pts[:1] + pts[2:3], 3, 5) is None
+
+
+def test_coherent_points_are_batched_through_the_simulator(monkeypatch, model):
+    """The coherent sampler runs a point's shots through Simulator batches of
+    at most max_shots, each at its own global shot offset, and concatenates
+    the device's detector rows in order (a stand-in simulator that encodes
+    the shot index in its detector row)."""
+    import paper_2605_29514_gb300 as pkg
+    from paper_2605_29514_gb300.sweep import coherent_sampler
+
+    calls = []
+
+    class FakeSim:
+        def __init__(self, w, max_shots):
+            self.max_shots = max_shots
+            self.n_det = 8
+
+        def sample_shots(self, n, offset, table, born=True, stats=True):
+            calls.append((n, offset))
+            self.cur = (n, offset)
+
+        def read_detectors(self):
+            n, off = self.cur
+            idx = np.arange(off, off + n)
+            det = ((idx[:, None] >> np.arange(8)) & 1).astype(np.uint8)
+            return det, (idx & 1).astype(np.uint8)
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(pkg, "Simulator", FakeSim)
+    det, obs = coherent_sampler(max_shots=64, shot_offset=1000)(D3_EXACT, 150, np.zeros(3))
+    assert calls == [(64, 1000), (64, 1064), (22, 1128)]
+    idx = np.arange(1000, 1150)
+    assert np.array_equal(det, ((idx[:, None] >> np.arange(8)) & 1).astype(np.uint8))
+    assert np.array_equal(obs, (idx & 1).astype(np.uint8))
